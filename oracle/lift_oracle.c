@@ -1,0 +1,600 @@
+/*
+ * FP64 CPU oracle for the lifted primal-dual (PDHG) solver of
+ * "Sublabel-Accurate Relaxation of Nonconvex Energies" (Moellenhoff, Laude,
+ * Moeller, Lellmann, Cremers, arXiv 1512.01383).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Every quantity is computed from its definition, in double precision:
+ *   - the data term rho(x,t) itself (quadratic, truncated quadratic, or the
+ *     piecewise-linear interpolant of sampled costs);
+ *   - the per-interval conjugate rho_i^*(y) = sup_{t in Gamma_i} t*y - rho(t)
+ *     (Prop. 1, with rho_i = rho + delta_{Gamma_i}), evaluated as an explicit
+ *     maximum over the few candidate maximisers of each smooth part;
+ *   - the Euclidean projection onto epi(rho_i^*), as the minimiser of the
+ *     convex 1-D function  y -> (y-y0)^2/2 + max(rho_i^*(y)-h0, 0)^2/2,
+ *     found by bisection on its monotone derivative;
+ *   - the convexified piece rho_i^** (t) = sup_y t*y - rho_i^*(y), again by
+ *     bisection on a monotone derivative;
+ *   - the PDHG iteration on the saddle-point problem of Sec. 4
+ *     (eq. discrete_saddle_point_final with the set C of eq. constraint_C,
+ *     the z-splitting of eq. equality_constr_data and its multiplier s,
+ *     the l2-ball set K of Prop. 5, forward differences on a Cartesian grid),
+ *     with the diagonal preconditioning of Pock-Chambolle (alpha = 1).
+ *
+ * Readings of points the paper leaves open (each also listed in the design doc):
+ *   c_i(v) = <1_{i-1}, v> - gamma_i v_i / Delta_i (appendix form, proof of
+ *   Prop. 1); lambda is the radius factor of K (|p_i| <= lambda*Delta_i);
+ *   Neumann forward differences; primal box u in [0,1]^k; fixed steps
+ *   (no adaptive step rule); dual step first from the extrapolated primal,
+ *   then primal step, then extrapolation with theta = 1; all variables start
+ *   at zero.
+ *
+ * Parity pins for every function here live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Problem description (owned by the caller, read-only here).               */
+/* ------------------------------------------------------------------------ */
+enum { ORC_QUAD = 0, ORC_TRUNC = 1, ORC_PL = 2 };
+
+typedef struct {
+    int kind;              /* ORC_QUAD: rho = alpha/2 (t-f)^2
+                              ORC_TRUNC: rho = min(alpha (t-f)^2, nu)
+                              ORC_PL: rho = PL interpolant of sampled costs */
+    int H, W, L;           /* image size, number of labels (k = L-1)      */
+    double gmin, gmax;     /* label range Gamma = [gmin, gmax], equidistant */
+    double lam;            /* TV weight lambda                             */
+    double alpha, nu;      /* data-term parameters                         */
+    const double *f;       /* H*W input image (QUAD, TRUNC)                */
+    const double *cost;    /* H*W*ns sampled costs, pixel-major (PL)       */
+    int ns;                /* number of samples per pixel (PL)             */
+    double smin, smax;     /* sample positions smin + j (smax-smin)/(ns-1)  */
+} orc_problem;
+
+/* PDHG state; all arrays caller-allocated, index [pixel*k + i]. */
+typedef struct {
+    double *u, *s;         /* primal: lifted u and multiplier s            */
+    double *ubar, *sbar;   /* extrapolated primal                          */
+    double *v, *z;         /* dual: data-term dual and scaled epigraph var */
+    double *px, *py;       /* dual: TV dual p_i in R^2                     */
+    double *q;             /* dual: epigraph height, one per pixel         */
+} orc_state;
+
+static double gam(const orc_problem *P, int j)   /* gamma_{j+1}, j = 0..k */
+{
+    int k = P->L - 1;
+    return P->gmin + (P->gmax - P->gmin) * (double)j / (double)k;
+}
+
+static double clampd(double x, double lo, double hi)
+{
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The data term rho(x, t) (eq. general_energy; Sec. 5.1, 5.2, 5.4).         */
+/* ------------------------------------------------------------------------ */
+static double pl_pos(const orc_problem *P, int j)
+{
+    return P->smin + (P->smax - P->smin) * (double)j / (double)(P->ns - 1);
+}
+
+double orc_rho(const orc_problem *P, int pix, double t)
+{
+    if (P->kind == ORC_QUAD) {
+        double d = t - P->f[pix];
+        return 0.5 * P->alpha * d * d;
+    }
+    if (P->kind == ORC_TRUNC) {
+        double d = t - P->f[pix];
+        double qd = P->alpha * d * d;
+        return qd < P->nu ? qd : P->nu;
+    }
+    /* piecewise-linear interpolation of the samples */
+    const double *c = P->cost + (size_t)pix * P->ns;
+    double h = (P->smax - P->smin) / (double)(P->ns - 1);
+    double x = (clampd(t, P->smin, P->smax) - P->smin) / h;
+    int j = (int)floor(x);
+    if (j < 0) j = 0;
+    if (j > P->ns - 2) j = P->ns - 2;
+    double a = x - (double)j;
+    return (1.0 - a) * c[j] + a * c[j + 1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* rho_i^*(y) = sup_{t in [gamma_i, gamma_{i+1}]} t*y - rho(t)  (Prop. 1).   */
+/* Returns the value; *tmax receives a maximiser (a subgradient of rho_i^*).  */
+/* ------------------------------------------------------------------------ */
+double orc_conj(const orc_problem *P, int pix, int i, double y, double *tmax)
+{
+    double l = gam(P, i), r = gam(P, i + 1);
+    double best, bt;
+    if (P->kind == ORC_QUAD) {
+        /* concave quadratic in t: stationary point f + y/alpha, clamped */
+        double t = clampd(P->f[pix] + y / P->alpha, l, r);
+        best = t * y - orc_rho(P, pix, t);
+        bt = t;
+    } else if (P->kind == ORC_TRUNC) {
+        /* -min(A,B) = max(-A,-B): the sup of the max is the max of the sups */
+        double f = P->f[pix];
+        double tq = clampd(f + y / (2.0 * P->alpha), l, r);
+        double vq = tq * y - P->alpha * (tq - f) * (tq - f);
+        double tc = y >= 0.0 ? r : l;
+        double vc = tc * y - P->nu;
+        if (vq >= vc) { best = vq; bt = tq; } else { best = vc; bt = tc; }
+    } else {
+        /* t*y - rho(t) is piecewise linear in t: the sup is attained at a
+           breakpoint of rho inside Gamma_i or at an end of Gamma_i */
+        best = l * y - orc_rho(P, pix, l);
+        bt = l;
+        for (int j = 0; j < P->ns; ++j) {
+            double t = pl_pos(P, j);
+            if (t > l && t < r) {
+                double val = t * y - orc_rho(P, pix, t);
+                if (val > best) { best = val; bt = t; }
+            }
+        }
+        double vr = r * y - orc_rho(P, pix, r);
+        if (vr > best) { best = vr; bt = r; }
+    }
+    if (tmax) *tmax = bt;
+    return best;
+}
+
+/* Lifted conjugate of Prop. 1:  max_i  c_i(v) + rho_i^*(v_i / Delta_i),
+   c_i(v) = sum_{l<i} v_l - gamma_i v_i / Delta_i (appendix form). */
+double orc_lifted_conj(const orc_problem *P, int pix, const double *v)
+{
+    int k = P->L - 1;
+    double best = -INFINITY, prefix = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double d = gam(P, i + 1) - gam(P, i);
+        double ci = prefix - gam(P, i) * v[i] / d;
+        double val = ci + orc_conj(P, pix, i, v[i] / d, NULL);
+        if (val > best) best = val;
+        prefix += v[i];
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Euclidean projection of (y0, h0) onto epi(rho_i^*) (Sec. 4, Fig. 7).      */
+/* Distance to the epigraph:  min_y (y-y0)^2 + max(phi(y)-h0, 0)^2, whose    */
+/* objective is convex in y; its derivative is monotone and is bisected.    */
+/* ------------------------------------------------------------------------ */
+static double epi_deriv(const orc_problem *P, int pix, int i, double y,
+                        double y0, double h0)
+{
+    double t;
+    double phi = orc_conj(P, pix, i, y, &t);
+    double e = phi - h0;
+    if (e < 0.0) e = 0.0;
+    return (y - y0) + e * t;
+}
+
+void orc_proj_epi(const orc_problem *P, int pix, int i, double y0, double h0,
+                  double *y_out, double *h_out)
+{
+    double phi0 = orc_conj(P, pix, i, y0, NULL);
+    if (h0 >= phi0) { *y_out = y0; *h_out = h0; return; }
+    /* the minimiser lies within the distance phi0-h0 of y0 */
+    double d0 = phi0 - h0;
+    double lo = y0 - d0, hi = y0 + d0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (epi_deriv(P, pix, i, mid, y0, h0) > 0.0) hi = mid; else lo = mid;
+    }
+    double y = 0.5 * (lo + hi);
+    double phi = orc_conj(P, pix, i, y, NULL);
+    *y_out = y;
+    *h_out = phi > h0 ? phi : h0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* rho_i^**(t) = sup_y t*y - rho_i^*(y), t in Gamma_i: the convexified piece */
+/* that the relaxation sees (Prop. 1 and the remark after it).               */
+/* ------------------------------------------------------------------------ */
+static double slope_bound(const orc_problem *P, int pix, int i)
+{
+    double l = gam(P, i), r = gam(P, i + 1);
+    if (P->kind == ORC_QUAD) {
+        double f = P->f[pix];
+        return 1.0 + P->alpha * (fabs(l - f) + fabs(r - f));
+    }
+    if (P->kind == ORC_TRUNC) {
+        double f = P->f[pix];
+        return 1.0 + 2.0 * P->alpha * (fabs(l - f) + fabs(r - f))
+                   + 2.0 * P->nu / (r - l);
+    }
+    /* PL: no slope of the lower hull exceeds the largest secant slope */
+    double m = 0.0, tp = l, rp = orc_rho(P, pix, l);
+    for (int j = 0; j <= P->ns; ++j) {
+        double t = j < P->ns ? pl_pos(P, j) : r;
+        if (j < P->ns && !(t > l && t < r)) continue;
+        double rv = orc_rho(P, pix, t);
+        double sl = fabs(rv - rp) / (t - tp);
+        if (sl > m) m = sl;
+        tp = t; rp = rv;
+    }
+    return 1.0 + 2.0 * m;
+}
+
+double orc_biconj(const orc_problem *P, int pix, int i, double t)
+{
+    double Y = slope_bound(P, pix, i);
+    double lo = -Y, hi = Y;
+    /* d/dy [t*y - rho_i^*(y)] = t - tmax(y), non-increasing in y */
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double tm;
+        orc_conj(P, pix, i, mid, &tm);
+        if (t - tm > 0.0) lo = mid; else hi = mid;
+    }
+    double y = 0.5 * (lo + hi);
+    return t * y - orc_conj(P, pix, i, y, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward differences with Neumann boundary (Sec. 4) and div = -grad^T.     */
+/* Arrays are [pixel*k + i].                                                 */
+/* ------------------------------------------------------------------------ */
+void orc_grad(int H, int W, int k, const double *u, double *gx, double *gy)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int i = 0; i < k; ++i) {
+                size_t o = ((size_t)y * W + x) * k + i;
+                gx[o] = x + 1 < W ? u[o + k] - u[o] : 0.0;
+                gy[o] = y + 1 < H ? u[o + (size_t)W * k] - u[o] : 0.0;
+            }
+}
+
+void orc_div(int H, int W, int k, const double *px, const double *py,
+             double *d)
+{
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int i = 0; i < k; ++i) {
+                size_t o = ((size_t)y * W + x) * k + i;
+                double a = 0.0;
+                if (x + 1 < W) a += px[o];
+                if (x > 0) a -= px[o - k];
+                if (y + 1 < H) a += py[o];
+                if (y > 0) a -= py[o - (size_t)W * k];
+                d[o] = a;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step sizes: diagonal preconditioning with alpha = 1, i.e. the reciprocal  */
+/* absolute row / column sums of the linear operator of the saddle point:   */
+/*   v_l : u_l + sum_{j>l} Delta_j s_j - gamma_l s_l                         */
+/*   z_i : s_i          q : -sum_i Delta_i s_i        p_i : grad u_i         */
+/* The (v_i, z_i) pair is projected jointly, so it shares one step (the      */
+/* smaller of its two rows); both components of p_i share 1/2; the column   */
+/* of u uses the interior count 1 + 4.                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double tau_u, sigma_q, sigma_p;
+    double *tau_s, *sigma_vz;
+} orc_steps;
+
+static void make_steps(const orc_problem *P, orc_steps *S)
+{
+    int k = P->L - 1;
+    S->tau_u = 1.0 / 5.0;
+    S->sigma_q = 1.0 / (gam(P, k) - gam(P, 0));
+    S->sigma_p = 0.5;
+    S->tau_s = (double *)malloc(sizeof(double) * k);
+    S->sigma_vz = (double *)malloc(sizeof(double) * k);
+    for (int i = 0; i < k; ++i) {
+        double d = gam(P, i + 1) - gam(P, i);
+        /* column of s_i: (i) entries Delta_i in v_l (l<i), |gamma_i| in v_i,
+           1 in z_i, Delta_i in q  (0-based i: i entries with l < i) */
+        S->tau_s[i] = 1.0 / (1.0 + fabs(gam(P, i)) + (double)(i + 1) * d);
+        double row_v = 1.0 + fabs(gam(P, i)) + (gam(P, k) - gam(P, i + 1));
+        double row_z = 1.0;
+        S->sigma_vz[i] = 1.0 / (row_v > row_z ? row_v : row_z);
+    }
+}
+
+static void free_steps(orc_steps *S)
+{
+    free(S->tau_s);
+    free(S->sigma_vz);
+}
+
+void orc_steps_get(const orc_problem *P, double *tau_u, double *sigma_q,
+                   double *sigma_p, double *tau_s, double *sigma_vz)
+{
+    orc_steps S;
+    make_steps(P, &S);
+    *tau_u = S.tau_u; *sigma_q = S.sigma_q; *sigma_p = S.sigma_p;
+    int k = P->L - 1;
+    for (int i = 0; i < k; ++i) { tau_s[i] = S.tau_s[i]; sigma_vz[i] = S.sigma_vz[i]; }
+    free_steps(&S);
+}
+
+/* ------------------------------------------------------------------------ */
+/* PDHG iterations (Sec. 4): dual ascent from the extrapolated primal, then  */
+/* the projections onto K (l2 balls, Prop. 5) and onto the scaled epigraphs */
+/* of rho_i^* (eq. equality_constr_data), then primal descent on (u, s)     */
+/* with u kept in [0,1]^k, then extrapolation with theta = 1.               */
+/* ------------------------------------------------------------------------ */
+int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
+{
+    int H = P->H, W = P->W, k = P->L - 1;
+    size_t N = (size_t)H * W, Nk = N * k;
+    orc_steps S;
+    make_steps(P, &S);
+    double *gx = (double *)malloc(sizeof(double) * Nk);
+    double *gy = (double *)malloc(sizeof(double) * Nk);
+    double *dv = (double *)malloc(sizeof(double) * Nk);
+    if (!gx || !gy || !dv) { free(gx); free(gy); free(dv); free_steps(&S); return -1; }
+
+    for (int n = 0; n < iters; ++n) {
+        /* ---- dual step ---- */
+        orc_grad(H, W, k, X->ubar, gx, gy);
+        for (size_t pix = 0; pix < N; ++pix) {
+            double *v = X->v + pix * k, *z = X->z + pix * k;
+            double *px = X->px + pix * k, *py = X->py + pix * k;
+            const double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
+            /* TV dual: ascent, then projection onto |p_i| <= lambda Delta_i */
+            for (int i = 0; i < k; ++i) {
+                double d = gam(P, i + 1) - gam(P, i);
+                double ax = px[i] + S.sigma_p * gx[pix * k + i];
+                double ay = py[i] + S.sigma_p * gy[pix * k + i];
+                double nrm = sqrt(ax * ax + ay * ay), R = P->lam * d;
+                double sc = nrm > R ? (nrm > 0.0 ? R / nrm : 0.0) : 1.0;
+                px[i] = ax * sc;
+                py[i] = ay * sc;
+            }
+            /* data duals: ascent on v, z, q */
+            double tot = 0.0;
+            for (int i = 0; i < k; ++i) tot += (gam(P, i + 1) - gam(P, i)) * sb[i];
+            for (int l = 0; l < k; ++l) {
+                double tail = 0.0;
+                for (int j = l + 1; j < k; ++j) tail += (gam(P, j + 1) - gam(P, j)) * sb[j];
+                v[l] += S.sigma_vz[l] * (ub[l] + tail - gam(P, l) * sb[l]);
+                z[l] += S.sigma_vz[l] * sb[l];
+            }
+            X->q[pix] -= S.sigma_q * (1.0 + tot);
+            /* projection of (v_i, z_i) onto Delta_i * epi(rho_i^*) */
+            for (int i = 0; i < k; ++i) {
+                double d = gam(P, i + 1) - gam(P, i);
+                double yo, ho;
+                orc_proj_epi(P, (int)pix, i, v[i] / d, z[i] / d, &yo, &ho);
+                v[i] = d * yo;
+                z[i] = d * ho;
+            }
+        }
+        /* ---- primal step ---- */
+        orc_div(H, W, k, X->px, X->py, dv);
+        for (size_t pix = 0; pix < N; ++pix) {
+            const double *v = X->v + pix * k, *z = X->z + pix * k;
+            double *u = X->u + pix * k, *s = X->s + pix * k;
+            double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
+            double q = X->q[pix], prefix = 0.0;
+            for (int i = 0; i < k; ++i) {
+                double d = gam(P, i + 1) - gam(P, i);
+                double un = clampd(u[i] - S.tau_u * (v[i] - dv[pix * k + i]), 0.0, 1.0);
+                double sn = s[i] - S.tau_s[i] * (z[i] - d * q + d * prefix - gam(P, i) * v[i]);
+                prefix += v[i];
+                ub[i] = 2.0 * un - u[i];
+                sb[i] = 2.0 * sn - s[i];
+                u[i] = un;
+                s[i] = sn;
+            }
+        }
+    }
+    free(gx); free(gy); free(dv);
+    free_steps(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Unlifting by the layer-cake formula (Sec. 3), on the clamped iterate.     */
+/* ------------------------------------------------------------------------ */
+void orc_unlift(const orc_problem *P, const double *u, double *out)
+{
+    int k = P->L - 1;
+    size_t N = (size_t)P->H * P->W;
+    for (size_t pix = 0; pix < N; ++pix) {
+        double a = gam(P, 0);
+        for (int i = 0; i < k; ++i)
+            a += clampd(u[pix * k + i], 0.0, 1.0) * (gam(P, i + 1) - gam(P, i));
+        out[pix] = a;
+    }
+}
+
+/* Projection onto {1 >= w_1 >= ... >= w_k >= 0}: pool adjacent violators for
+   the non-increasing order, then clamp to [0,1]. */
+void orc_monotone_proj(int k, const double *u, double *w)
+{
+    double *val = (double *)malloc(sizeof(double) * k);
+    int *cnt = (int *)malloc(sizeof(int) * k);
+    int nb = 0;
+    for (int i = 0; i < k; ++i) {
+        val[nb] = u[i];
+        cnt[nb] = 1;
+        ++nb;
+        while (nb > 1 && val[nb - 2] < val[nb - 1]) {
+            double tot = val[nb - 2] * cnt[nb - 2] + val[nb - 1] * cnt[nb - 1];
+            cnt[nb - 2] += cnt[nb - 1];
+            val[nb - 2] = tot / cnt[nb - 2];
+            --nb;
+        }
+    }
+    int o = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < cnt[b]; ++c) w[o++] = clampd(val[b], 0.0, 1.0);
+    free(val);
+    free(cnt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energies.                                                                 */
+/*  D   : dual bound.  With p in K and q(x) = max_i rho_i^*(v(x)) (the        */
+/*        smallest q allowed by C), minimising the Lagrangian over            */
+/*        u in [0,1]^k gives sum_x sum_i min(0, v_i - (div p)_i) - q(x).      */
+/*  Phat: relaxed energy of an explicit feasible point.  u is projected onto  */
+/*        the monotone set; its data term is bounded by a decomposition of    */
+/*        u into points of the graph pieces, u = sum_i lam_i 1_i^{a_i}, whose */
+/*        tail sums S_i = sum_{j>=i} lam_j must interleave u (S_{i+1} <= u_i  */
+/*        <= S_i).  The masses come from the multiplier s (-Delta_i s_i),     */
+/*        clamped into the interleaving intervals; the TV term is             */
+/*        lambda sum_i Delta_i |grad u_i| (Prop. 5).                          */
+/*  Enc : nonconvex energy of the unlifted image,                             */
+/*        sum_x rho(x, u~) + lambda sum_x |grad u~|_2.                        */
+/* ------------------------------------------------------------------------ */
+void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
+                double *Dual, double *Enc)
+{
+    int H = P->H, W = P->W, k = P->L - 1;
+    size_t N = (size_t)H * W, Nk = N * k;
+    double *dv = (double *)malloc(sizeof(double) * Nk);
+    double *uf = (double *)malloc(sizeof(double) * Nk);
+    double *gx = (double *)malloc(sizeof(double) * Nk);
+    double *gy = (double *)malloc(sizeof(double) * Nk);
+    double *ut = (double *)malloc(sizeof(double) * N);
+    double *S = (double *)malloc(sizeof(double) * (k + 1));
+
+    /* dual bound */
+    orc_div(H, W, k, X->px, X->py, dv);
+    double D = 0.0;
+    for (size_t pix = 0; pix < N; ++pix) {
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double g = X->v[pix * k + i] - dv[pix * k + i];
+            a += g < 0.0 ? g : 0.0;
+        }
+        a -= orc_lifted_conj(P, (int)pix, X->v + pix * k);
+        D += a;
+    }
+
+    /* primal bound */
+    double Pd = 0.0;
+    for (size_t pix = 0; pix < N; ++pix) {
+        const double *s = X->s + pix * k;
+        double *w = uf + pix * k;
+        orc_monotone_proj(k, X->u + pix * k, w);
+        S[0] = 1.0;
+        S[k] = 0.0;
+        double tail = 0.0;
+        for (int i = k - 1; i >= 1; --i) {
+            tail += -(gam(P, i + 1) - gam(P, i)) * s[i];
+            S[i] = clampd(tail, w[i], w[i - 1]);
+        }
+        for (int i = 0; i < k; ++i) {
+            double li = S[i] - S[i + 1];
+            if (li <= 0.0) continue;
+            double a = clampd((w[i] - S[i + 1]) / li, 0.0, 1.0);
+            double d = gam(P, i + 1) - gam(P, i);
+            Pd += li * orc_biconj(P, (int)pix, i, gam(P, i) + a * d);
+        }
+    }
+    orc_grad(H, W, k, uf, gx, gy);
+    double tv = 0.0;
+    for (size_t o = 0; o < Nk; ++o) {
+        int i = (int)(o % k);
+        tv += (gam(P, i + 1) - gam(P, i)) * sqrt(gx[o] * gx[o] + gy[o] * gy[o]);
+    }
+    Pd += P->lam * tv;
+
+    /* nonconvex energy of the unlifted image */
+    orc_unlift(P, X->u, ut);
+    double E = 0.0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t pix = (size_t)y * W + x;
+            double ax = x + 1 < W ? ut[pix + 1] - ut[pix] : 0.0;
+            double ay = y + 1 < H ? ut[pix + W] - ut[pix] : 0.0;
+            E += orc_rho(P, (int)pix, ut[pix]) + P->lam * sqrt(ax * ax + ay * ay);
+        }
+
+    *Phat = Pd;
+    *Dual = D;
+    *Enc = E;
+    free(dv); free(uf); free(gx); free(gy); free(ut); free(S);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independent side solver: box-constrained ROF, unlifted,                   */
+/*   min_{u in [lo,hi]} sum alpha/2 (u-f)^2 + lambda sum |grad u|_2,         */
+/* by the accelerated primal-dual method of Chambolle and Pock (their        */
+/* Algorithm 2, strong convexity alpha).  Used only to pin Prop. 3 (L = 2)   */
+/* and the tightness of the relaxation for convex data terms.               */
+/* Returns the final primal-dual gap.                                        */
+/* ------------------------------------------------------------------------ */
+static double rof_primal(int H, int W, const double *u, const double *f,
+                         double alpha, double lam)
+{
+    double e = 0.0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t o = (size_t)y * W + x;
+            double ax = x + 1 < W ? u[o + 1] - u[o] : 0.0;
+            double ay = y + 1 < H ? u[o + W] - u[o] : 0.0;
+            e += 0.5 * alpha * (u[o] - f[o]) * (u[o] - f[o]) + lam * sqrt(ax * ax + ay * ay);
+        }
+    return e;
+}
+
+double orc_rof_direct(int H, int W, const double *f, double alpha, double lam,
+                      double lo, double hi, int iters, double *u)
+{
+    size_t N = (size_t)H * W;
+    double *px = (double *)calloc(N, sizeof(double));
+    double *py = (double *)calloc(N, sizeof(double));
+    double *ub = (double *)malloc(sizeof(double) * N);
+    double *dv = (double *)malloc(sizeof(double) * N);
+    double *gx = (double *)malloc(sizeof(double) * N);
+    double *gy = (double *)malloc(sizeof(double) * N);
+    for (size_t o = 0; o < N; ++o) { u[o] = clampd(f[o], lo, hi); ub[o] = u[o]; }
+    double tau = 1.0 / sqrt(8.0), sigma = 1.0 / sqrt(8.0);
+    for (int n = 0; n < iters; ++n) {
+        orc_grad(H, W, 1, ub, gx, gy);
+        for (size_t o = 0; o < N; ++o) {
+            double ax = px[o] + sigma * gx[o], ay = py[o] + sigma * gy[o];
+            double nrm = sqrt(ax * ax + ay * ay);
+            double sc = nrm > lam ? (nrm > 0.0 ? lam / nrm : 0.0) : 1.0;
+            px[o] = ax * sc;
+            py[o] = ay * sc;
+        }
+        orc_div(H, W, 1, px, py, dv);
+        double theta = 1.0 / sqrt(1.0 + 2.0 * alpha * tau);
+        for (size_t o = 0; o < N; ++o) {
+            double un = (u[o] + tau * dv[o] + tau * alpha * f[o]) / (1.0 + tau * alpha);
+            un = clampd(un, lo, hi);
+            ub[o] = un + theta * (un - u[o]);
+            u[o] = un;
+        }
+        tau *= theta;
+        sigma /= theta;
+    }
+    /* gap: primal energy minus the dual objective of the box-constrained
+       problem, min_{u in box} alpha/2 (u-f)^2 - u*div p, per pixel */
+    orc_div(H, W, 1, px, py, dv);
+    double dual = 0.0;
+    for (size_t o = 0; o < N; ++o) {
+        double t = clampd(f[o] + dv[o] / alpha, lo, hi);
+        dual += 0.5 * alpha * (t - f[o]) * (t - f[o]) - t * dv[o];
+    }
+    double gap = rof_primal(H, W, u, f, alpha, lam) - dual;
+    free(px); free(py); free(ub); free(dv); free(gx); free(gy);
+    return gap;
+}
+
+double orc_rof_energy(int H, int W, const double *u, const double *f,
+                      double alpha, double lam)
+{
+    return rof_primal(H, W, u, f, alpha, lam);
+}

@@ -1,0 +1,257 @@
+"""ctypes binding of the FP64 oracle (``lift_oracle.c``).
+
+Test infrastructure only: callers are ``tests/``, ``__graft_entry__.smoke()``
+and the CPU legs of ``bench.py``.  The library is compiled from source with
+gcc on first use (or by ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+QUAD, TRUNC, PL = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lift_oracle.c")
+_SO = os.path.join(_HERE, "liblift_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("H", C.c_int), ("W", C.c_int), ("L", C.c_int),
+        ("gmin", C.c_double), ("gmax", C.c_double), ("lam", C.c_double),
+        ("alpha", C.c_double), ("nu", C.c_double),
+        ("f", _dp), ("cost", _dp), ("ns", C.c_int),
+        ("smin", C.c_double), ("smax", C.c_double),
+    ]
+
+
+class _State(C.Structure):
+    _fields_ = [(n, _dp) for n in ("u", "s", "ubar", "sbar", "v", "z", "px", "py", "q")]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no fast-math)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            tmp = _SO + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P, S = C.POINTER(_Problem), C.POINTER(_State)
+        lib.orc_rho.restype = C.c_double
+        lib.orc_rho.argtypes = [P, C.c_int, C.c_double]
+        lib.orc_conj.restype = C.c_double
+        lib.orc_conj.argtypes = [P, C.c_int, C.c_int, C.c_double, _dp]
+        lib.orc_lifted_conj.restype = C.c_double
+        lib.orc_lifted_conj.argtypes = [P, C.c_int, _dp]
+        lib.orc_proj_epi.restype = None
+        lib.orc_proj_epi.argtypes = [P, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+        lib.orc_biconj.restype = C.c_double
+        lib.orc_biconj.argtypes = [P, C.c_int, C.c_int, C.c_double]
+        lib.orc_grad.restype = None
+        lib.orc_grad.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
+        lib.orc_div.restype = None
+        lib.orc_div.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
+        lib.orc_steps_get.restype = None
+        lib.orc_steps_get.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
+        lib.orc_pdhg.restype = C.c_int
+        lib.orc_pdhg.argtypes = [P, S, C.c_int]
+        lib.orc_unlift.restype = None
+        lib.orc_unlift.argtypes = [P, _dp, _dp]
+        lib.orc_monotone_proj.restype = None
+        lib.orc_monotone_proj.argtypes = [C.c_int, _dp, _dp]
+        lib.orc_energy.restype = None
+        lib.orc_energy.argtypes = [P, S, _dp, _dp, _dp]
+        lib.orc_rof_direct.restype = C.c_double
+        lib.orc_rof_direct.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double,
+                                       C.c_double, C.c_double, C.c_int, _dp]
+        lib.orc_rof_energy.restype = C.c_double
+        lib.orc_rof_energy.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return C.cast(None, _dp)
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def labels(L: int, gmin: float, gmax: float) -> np.ndarray:
+    """Equidistant labels gamma_1 < ... < gamma_L on [gmin, gmax] (Sec. 3)."""
+    k = L - 1
+    return gmin + (gmax - gmin) * np.arange(L, dtype=np.float64) / k
+
+
+@dataclass
+class Problem:
+    """Lifted problem: data term, label grid and TV weight (eq. general_energy)."""
+    kind: int
+    H: int
+    W: int
+    L: int
+    gmin: float = 0.0
+    gmax: float = 1.0
+    lam: float = 0.0
+    alpha: float = 1.0
+    nu: float = 0.0
+    f: np.ndarray | None = None
+    cost: np.ndarray | None = None
+    smin: float = 0.0
+    smax: float = 1.0
+    _c: _Problem = field(default=None, repr=False)
+
+    def __post_init__(self):
+        if self.f is not None:
+            self.f = np.ascontiguousarray(self.f, dtype=np.float64).reshape(self.H * self.W)
+        if self.cost is not None:
+            self.cost = np.ascontiguousarray(self.cost, dtype=np.float64).reshape(self.H * self.W, -1)
+        ns = 0 if self.cost is None else self.cost.shape[1]
+        self._c = _Problem(self.kind, self.H, self.W, self.L, self.gmin, self.gmax, self.lam,
+                           self.alpha, self.nu, _ptr(self.f), _ptr(self.cost), ns,
+                           self.smin, self.smax)
+
+    @property
+    def k(self) -> int:
+        return self.L - 1
+
+    @property
+    def N(self) -> int:
+        return self.H * self.W
+
+    def ref(self):
+        return C.byref(self._c)
+
+
+class State:
+    """PDHG iterate, all variables zero at the start (arrays [pixel, i])."""
+    names = ("u", "s", "ubar", "sbar", "v", "z", "px", "py")
+
+    def __init__(self, P: Problem):
+        for n in self.names:
+            setattr(self, n, np.zeros((P.N, P.k), dtype=np.float64))
+        self.q = np.zeros(P.N, dtype=np.float64)
+
+    def _c(self):
+        return _State(*[_ptr(getattr(self, n)) for n in self.names], _ptr(self.q))
+
+    def copy(self, P: Problem) -> "State":
+        o = State(P)
+        for n in self.names + ("q",):
+            getattr(o, n)[...] = getattr(self, n)
+        return o
+
+
+def rho(P: Problem, pix: int, t: float) -> float:
+    return _load().orc_rho(P.ref(), pix, t)
+
+
+def conj(P: Problem, pix: int, i: int, y: float) -> tuple[float, float]:
+    """(rho_i^*(y), a maximiser t) for interval i (0-based) at pixel pix."""
+    t = C.c_double()
+    val = _load().orc_conj(P.ref(), pix, i, y, C.byref(t))
+    return val, t.value
+
+
+def lifted_conj(P: Problem, pix: int, v: np.ndarray) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return _load().orc_lifted_conj(P.ref(), pix, _ptr(v))
+
+
+def proj_epi(P: Problem, pix: int, i: int, y0: float, h0: float) -> tuple[float, float]:
+    y, h = C.c_double(), C.c_double()
+    _load().orc_proj_epi(P.ref(), pix, i, y0, h0, C.byref(y), C.byref(h))
+    return y.value, h.value
+
+
+def biconj(P: Problem, pix: int, i: int, t: float) -> float:
+    return _load().orc_biconj(P.ref(), pix, i, t)
+
+
+def grad(H: int, W: int, k: int, u: np.ndarray):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    gx, gy = np.empty_like(u), np.empty_like(u)
+    _load().orc_grad(H, W, k, _ptr(u), _ptr(gx), _ptr(gy))
+    return gx, gy
+
+
+def div(H: int, W: int, k: int, px: np.ndarray, py: np.ndarray):
+    px = np.ascontiguousarray(px, dtype=np.float64)
+    py = np.ascontiguousarray(py, dtype=np.float64)
+    d = np.empty_like(px)
+    _load().orc_div(H, W, k, _ptr(px), _ptr(py), _ptr(d))
+    return d
+
+
+def steps(P: Problem) -> dict:
+    tu, sq, sp = C.c_double(), C.c_double(), C.c_double()
+    ts, svz = np.zeros(P.k), np.zeros(P.k)
+    _load().orc_steps_get(P.ref(), C.byref(tu), C.byref(sq), C.byref(sp), _ptr(ts), _ptr(svz))
+    return {"tau_u": tu.value, "sigma_q": sq.value, "sigma_p": sp.value,
+            "tau_s": ts, "sigma_vz": svz}
+
+
+def pdhg(P: Problem, X: State, iters: int) -> State:
+    """Run ``iters`` PDHG iterations in place on X."""
+    cs = X._c()
+    rc = _load().orc_pdhg(P.ref(), C.byref(cs), iters)
+    if rc != 0:
+        raise MemoryError("oracle pdhg: allocation failed")
+    return X
+
+
+def unlift(P: Problem, u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(P.N)
+    _load().orc_unlift(P.ref(), _ptr(u), _ptr(out))
+    return out
+
+
+def monotone_proj(u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.empty_like(u)
+    _load().orc_monotone_proj(u.size, _ptr(u), _ptr(w))
+    return w
+
+
+def energy(P: Problem, X: State) -> tuple[float, float, float]:
+    """(P_hat, D, E_nc): primal bound, dual bound, nonconvex energy."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    cs = X._c()
+    _load().orc_energy(P.ref(), C.byref(cs), C.byref(a), C.byref(b), C.byref(c))
+    return a.value, b.value, c.value
+
+
+def rof_direct(f: np.ndarray, alpha: float, lam: float, lo: float, hi: float,
+               iters: int) -> tuple[np.ndarray, float]:
+    """Unlifted box-constrained ROF by accelerated primal-dual; (u, gap)."""
+    H, W = f.shape
+    fd = np.ascontiguousarray(f, dtype=np.float64)
+    u = np.empty_like(fd)
+    gap = _load().orc_rof_direct(H, W, _ptr(fd), alpha, lam, lo, hi, iters, _ptr(u))
+    return u, gap
+
+
+def rof_energy(u: np.ndarray, f: np.ndarray, alpha: float, lam: float) -> float:
+    H, W = f.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    fd = np.ascontiguousarray(f, dtype=np.float64)
+    return _load().orc_rof_energy(H, W, _ptr(u), _ptr(fd), alpha, lam)
