@@ -1,0 +1,333 @@
+"""Throughput of the lifted PDHG solver on one GB300 (or N replicas).
+
+Workload (one "step"): the robust truncated-quadratic denoising problem,
+512x512 pixels, rho = min(25 (u - f)^2, 0.1), lambda = 0.25, labels on [0,1]
+with L = 20 (k = 19 intervals): 100 PDHG iterations (dual step + primal step
+each), one FP64 energy / primal-dual gap evaluation and one unlift into a
+device buffer -- one check interval of lift_solve.  Inputs are synthetic
+(seeded Voronoi ramps + Gaussian noise + 10 % outliers).  The solver state
+(160 MB) and the bytes streamed per iteration (403 MB) exceed the 129 MB L2.
+
+Metric: pixel * k * iterations per second (whole job, all ranks).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own replica (weak scaling, no data
+exchange); the timed region is bracketed by barriers and the max over ranks
+is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 512
+L = 20
+K_INT = L - 1
+ALPHA, NU, LAM = 25.0, 0.1, 0.25
+ITERS_PER_STEP = 100
+SEED = 1512013831
+METRIC = "lifted PDHG Gpix·label·iter/s"
+UNIT = "Gpix*k*iter/s"
+WORKLOAD = ("truncated-quadratic denoising 512x512, L=20 (k=19), alpha=25 nu=0.1 lambda=0.25; "
+            "step = 100 PDHG iterations + FP64 gap check + unlift")
+# Algorithmic DRAM bytes per pixel and launch (float32 records):
+#   dual step  : read xbar 8k + dual 16k + f 4 + q 4, write dual 16k + q 4 = 40k + 12
+#   primal step: read primal 8k + dual 16k + q 4, write primal 8k + xbar 8k = 40k + 4
+DUAL_BYTES_PER_PIX = 40 * K_INT + 12
+PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
+# DRAM bytes per dual-step launch from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), profiles/dual_step_trunc512_L20.md; None when the
+# kernel has changed since the capture.
+DUAL_TRAFFIC_NCU = None
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d and isinstance(d[key], (int, float)):
+                    return float(d[key]), "measured"
+        except Exception:
+            pass
+    return PEAK_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(rank: int = 0):
+    from paper_1512_01383_gb300 import synth
+    f, _ = synth.voronoi_ramps(H, W, SEED + rank)
+    return synth.as_f32(f)
+
+
+def cpu_sample(f: np.ndarray, side: int, iters: int):
+    """Time the FP64 oracle on a side x side crop of the workload."""
+    import oracle as O
+    crop = np.ascontiguousarray(f[:side, :side]).astype(np.float64)
+    P = O.Problem(O.TRUNC, side, side, L, 0.0, 1.0, lam=LAM, alpha=ALPHA, nu=NU, f=crop)
+    X = O.State(P)
+    t0 = time.perf_counter()
+    O.pdhg(P, X, iters)
+    O.energy(P, X)
+    O.unlift(P, X.u)
+    dt = time.perf_counter() - t0
+    units = side * side * K_INT * iters
+    return units / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    f = make_input(0)
+    side, iters = 64, 20
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, _ = cpu_sample(f, side, iters)
+        if s >= args.warmup:
+            vals.append(v)
+    units = side * side * K_INT * iters
+    value = units * len(vals) / sum(units / v for v in vals)
+    sample = f"{side}x{side} crop of the workload, L={L}, {iters} PDHG iterations + energy + unlift per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * units / (value * 1e9), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap runs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    import torch
+    from paper_1512_01383_gb300 import lift as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    f = make_input(rank)
+    fd = torch.from_numpy(f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = G.Solver(G.LIFT_TRUNC_QUAD, H, W, L, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
+                      check_every=ITERS_PER_STEP, stream=stream.cuda_stream)
+    uout = torch.empty((H, W), device=dev)
+    energy_buf = []
+
+    def step():
+        solver.iterate(ITERS_PER_STEP)
+        energy_buf.append(solver.energy())       # FP64 gap check (syncs 24 bytes)
+        solver.unlift(uout)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    units = H * W * K_INT * ITERS_PER_STEP * args.steps * world
+    value = units / (ms * 1e-3) / 1e9
+
+    # per-kernel durations with events on the launching stream
+    nk = 200
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * nk)]
+    barrier()
+    for j in range(nk):
+        ev[3 * j].record(stream)
+        G.lift_dual_step(solver.h)
+        ev[3 * j + 1].record(stream)
+        G.lift_primal_step(solver.h)
+        ev[3 * j + 2].record(stream)
+    torch.cuda.synchronize()
+    dual_ms = statistics.median(ev[3 * j].elapsed_time(ev[3 * j + 1]) for j in range(nk))
+    primal_ms = statistics.median(ev[3 * j + 1].elapsed_time(ev[3 * j + 2]) for j in range(nk))
+    peak, peak_kind = peaks()
+    dual_gbs = DUAL_BYTES_PER_PIX * H * W / (dual_ms * 1e-3) / 1e9
+    primal_gbs = PRIMAL_BYTES_PER_PIX * H * W / (primal_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: upload f from pinned
+    # host memory, reset, iterate, gap check, unlift to host
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty((H, W), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        solver.set_data(fh)
+        solver.reset()
+        solver.iterate(ITERS_PER_STEP)
+        solver.energy()
+        solver.unlift(uh)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_value = units / float(tt.item()) / 1e9
+
+    # time to relative gap 1e-5 (outside the timed region, per L)
+    ttg = {}
+    if not args.no_ttg and rank == 0:
+        for Lx in (5, 10, 20):
+            with G.Solver(G.LIFT_TRUNC_QUAD, H, W, Lx, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
+                          check_every=250, stream=stream.cuda_stream) as s2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, n = s2.solve(60000, 1e-5)
+                dt = time.perf_counter() - t0
+                ttg[f"L{Lx}"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
+                                 "rel_gap": s2.gap()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        side, iters = 96, 50
+        v, dt = cpu_sample(f, side, iters)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{side}x{side} crop, L={L}, {iters} iterations + energy + unlift ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "k": K_INT,
+                       "iters_per_step": ITERS_PER_STEP, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (160 MB state, 403 MB per iteration)"},
+            "roofline": {"bound": "hbm", "kernel": "dual_step_kernel", "achieved": dual_gbs,
+                         "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                         "frac": dual_gbs / peak, "traffic": DUAL_TRAFFIC_NCU,
+                         "algorithmic_bytes_per_launch": DUAL_BYTES_PER_PIX * H * W,
+                         "launch_ms": dual_ms,
+                         "primal_step": {"achieved": primal_gbs, "frac": primal_gbs / peak,
+                                         "launch_ms": primal_ms,
+                                         "algorithmic_bytes_per_launch": PRIMAL_BYTES_PER_PIX * H * W}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
+                    "d2h_bytes_per_step": H * W * 4 + 24},
+            "gpu_launches": args.steps * (2 * ITERS_PER_STEP + 3),
+            "clocks": clk.summary(),
+            "time_to_gap_1e-5": ttg or None,
+            "final_energy": {"primal": energy_buf[-1][0], "dual": energy_buf[-1][1],
+                             "nonconvex": energy_buf[-1][2]},
+        }
+        print(json.dumps(line))
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

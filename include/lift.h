@@ -1,0 +1,185 @@
+/*
+ * lift.h -- C ABI of the GB300 (sm_103a) solver for the sublabel-accurate
+ * convex relaxation of Moellenhoff, Laude, Moeller, Lellmann, Cremers,
+ * "Sublabel-Accurate Relaxation of Nonconvex Energies" (arXiv 1512.01383).
+ *
+ * The library minimises the relaxed energy of Sec. 4,
+ *     min_u  sum_x rho^**(x, u(x)) + Phi^**(grad u(x)),
+ * over the lifted variable u : Omega -> R^k (k = L-1 label intervals) by the
+ * preconditioned primal-dual method of Sec. 4 on the saddle-point problem
+ * (eq. discrete_saddle_point_final) with the z-splitting of
+ * eq. equality_constr_data and its multiplier s.  Each iteration is two
+ * fused kernels: a dual step (forward-difference gradient, projection onto
+ * the l2 balls of Prop. 5, projection onto the epigraphs of rho_i^*) and a
+ * primal step (divergence, primal descent, box clamp, extrapolation).
+ *
+ * Conventions for every entry point:
+ *  - Return value: LIFT_OK (0) or one of the LIFT_ERR_* codes below;
+ *    lift_strerror() names it.  A failed call leaves the handle usable
+ *    unless it returned LIFT_ERR_CUDA (sticky CUDA error: destroy it).
+ *  - All GPU work is issued on the handle's stream, in call order.  Calls
+ *    that return host values (lift_energy, lift_gap, lift_solve, and any
+ *    call with on_host = 1) synchronise that stream before returning.
+ *  - "Device pointer" means memory of the current CUDA device; "host
+ *    pointer" means ordinary (pageable or pinned) host memory.
+ *  - The handle owns all solver state.  Input buffers are read during the
+ *    call that receives them and are not retained.  Output buffers are
+ *    allocated by the caller.
+ *  - A handle must not be used from two host threads at once.
+ */
+#ifndef LIFT_H
+#define LIFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define LIFT_OK                 0
+#define LIFT_ERR_SPEC           1  /* invalid problem description           */
+#define LIFT_ERR_OOM            2  /* device allocation failed              */
+#define LIFT_ERR_CUDA           3  /* a CUDA call failed                    */
+#define LIFT_ERR_NAN            4  /* non-finite energy: iterate diverged   */
+#define LIFT_ERR_NOT_CONVERGED  5  /* max_iters reached before gap <= tol   */
+#define LIFT_ERR_ARG            6  /* invalid argument (null, size, range)  */
+
+/* Largest supported number of label intervals k = L-1. */
+#define LIFT_MAX_K 64
+
+/* ---------------------------------------------------------- data terms */
+/* The data term rho(x, t) of eq. general_energy, t in Gamma = [gamma_min,
+ * gamma_max]:
+ *  LIFT_QUAD       rho = alpha/2 (t - f(x))^2          (Sec. 5.1 ROF)
+ *  LIFT_TRUNC_QUAD rho = min(alpha (t - f(x))^2, nu)   (Sec. 5.2)
+ *  LIFT_PL_SAMPLED rho = piecewise-linear interpolant of n_samples costs
+ *                  at positions sample_min + j (sample_max-sample_min)/
+ *                  (n_samples-1)                        (Sec. 5.4 stereo)
+ * Each interval Gamma_i = [gamma_i, gamma_{i+1}] sees only the convex
+ * envelope rho_i^** of rho restricted to it (Prop. 1).  For the two
+ * quadratic kinds the envelope is linear-quadratic-linear and is derived in
+ * closed form per pixel on the fly; for LIFT_PL_SAMPLED it is the lower
+ * convex hull of the samples inside each interval, computed once by
+ * lift_create / lift_set_data (the gift-wrapping step of Sec. 5.4). */
+#define LIFT_QUAD        0
+#define LIFT_TRUNC_QUAD  1
+#define LIFT_PL_SAMPLED  2
+
+typedef struct lift_spec {
+    int kind;                 /* LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED  */
+    int H, W;                 /* image size, H*W >= 1                        */
+    int L;                    /* labels, 2 <= L <= LIFT_MAX_K + 1            */
+    double gamma_min;         /* equidistant labels gamma_1 < ... < gamma_L  */
+    double gamma_max;         /*   on [gamma_min, gamma_max] (Sec. 3)         */
+    double lambda;            /* TV weight >= 0: ball radius lambda*Delta_i  */
+    double alpha, nu;         /* QUAD: alpha > 0.  TRUNC: alpha > 0, nu > 0  */
+    const float *f;           /* QUAD/TRUNC: H*W row-major image             */
+    const float *cost;        /* PL: H*W*n_samples, pixel-major              */
+    int n_samples;            /* PL: >= 2                                    */
+    double sample_min;        /* PL: sample positions; must cover Gamma      */
+    double sample_max;
+    int data_on_host;         /* 1: f / cost are host pointers, else device */
+    int check_every;          /* lift_solve: iterations between gap checks  */
+} lift_spec;
+
+typedef struct lift_ctx *lift_handle;
+
+/* lift_create: validate *spec, allocate the solver state on the current
+ * device, upload / convexify the data term and zero the iterate (all primal
+ * and dual variables start at 0).  stream: a cudaStream_t (NULL = legacy
+ * default stream) on which every later call of this handle runs.
+ * Errors: LIFT_ERR_ARG (null pointer), LIFT_ERR_SPEC (see lift_spec),
+ * LIFT_ERR_OOM, LIFT_ERR_CUDA. */
+int lift_create(const lift_spec *spec, void *stream, lift_handle *out);
+
+/* lift_destroy: free all device memory of the handle (synchronises its
+ * stream first).  NULL is ignored. */
+void lift_destroy(lift_handle h);
+
+/* lift_set_data: replace the data of an existing handle (same kind and
+ * sizes): f (H*W) for the quadratic kinds or cost (H*W*n_samples) for
+ * LIFT_PL_SAMPLED, from host (on_host = 1) or device memory.  Re-runs the
+ * per-pixel setup.  The iterate is not touched (call lift_reset). */
+int lift_set_data(lift_handle h, const float *data, int on_host);
+
+/* lift_reset: set every primal and dual variable to 0. */
+int lift_reset(lift_handle h);
+
+/* lift_iterate: run exactly `iters` >= 0 PDHG iterations (Sec. 4), each a
+ * dual step from the extrapolated primal followed by a primal step with
+ * extrapolation theta = 1.  Asynchronous: returns after enqueueing. */
+int lift_iterate(lift_handle h, int iters);
+
+/* lift_dual_step / lift_primal_step: one half-step each, the two kernels
+ * that lift_iterate runs per iteration (dual first, then primal).  Exposed
+ * so that callers can time or interleave them.  Asynchronous. */
+int lift_dual_step(lift_handle h);
+int lift_primal_step(lift_handle h);
+
+/* lift_solve: iterate until the relative primal-dual gap (see lift_gap) is
+ * <= rel_gap_tol, checking every spec->check_every iterations, or until
+ * max_iters iterations.  rel_gap_tol <= 0 runs max_iters iterations with no
+ * check.  *iters_done (may be NULL) receives the count.  Returns
+ * LIFT_ERR_NOT_CONVERGED if the tolerance was not met, LIFT_ERR_NAN if an
+ * energy became non-finite. */
+int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done);
+
+/* lift_energy: evaluate, with FP64 reductions over FP32 per-pixel terms:
+ *   primal_relaxed  an upper bound on the relaxed optimum: the relaxed
+ *                   energy of the current u projected onto the monotone
+ *                   set 1 >= u_1 >= ... >= u_k >= 0, with its data term
+ *                   bounded through the decomposition into graph pieces
+ *                   whose masses come from the multiplier s (Prop. 1);
+ *   dual            a lower bound on the relaxed optimum: the Lagrangian of
+ *                   eq. discrete_saddle_point_final minimised over u in
+ *                   [0,1]^k at the current p and v, with the smallest q
+ *                   allowed by the set C (eq. constraint_C);
+ *   e_nonconvex     sum_x rho(x, u~(x)) + lambda sum_x |grad u~(x)|_2 of
+ *                   the unlifted image u~ (lift_unlift).
+ * Any output pointer may be NULL.  Synchronises the stream. */
+int lift_energy(lift_handle h, double *primal_relaxed, double *dual,
+                double *e_nonconvex);
+
+/* lift_gap: (primal_relaxed - dual) / max(|primal_relaxed|, |dual|, 1). */
+int lift_gap(lift_handle h, double *rel_gap);
+
+/* lift_unlift: u~(x) = gamma_1 + sum_i clamp(u_i(x), 0, 1) Delta_i (the
+ * layer-cake formula of Sec. 3) into out[H*W] (row-major), a device pointer
+ * (on_host = 0, asynchronous) or a host pointer (on_host = 1). */
+int lift_unlift(lift_handle h, float *out, int on_host);
+
+/* State image for checkpoint / resume and for tests.  Layout (bytes, in
+ * this order, all float32, pixel p = y*W + x, interval i = 0..k-1):
+ *   primal  [H*W][k] float2 {u_i, s_i}
+ *   xbar    [H*W][k] float2 {ubar_i, sbar_i}   (extrapolated primal)
+ *   dual    [H*W][k] float4 {v_i, z_i, px_i, py_i}
+ *   q       [H*W]    float
+ * lift_state_bytes returns the total size.  get/set copy exactly that many
+ * bytes (bytes must equal it, else LIFT_ERR_ARG). */
+size_t lift_state_bytes(lift_handle h);
+int lift_get_state(lift_handle h, void *dst, size_t bytes, int on_host);
+int lift_set_state(lift_handle h, const void *src, size_t bytes, int on_host);
+
+/* lift_proj_epi: the projection used inside the dual step, exposed for
+ * testing: for n points, project (y0[j], h0[j]) onto epi(rho_i^*) of pixel
+ * pix[j] and interval interval[j] (0-based), where rho_i^*(y) =
+ * sup_{t in Gamma_i} t*y - rho(x, t) (Prop. 1, Fig. 7), writing y[j], h[j].
+ * All six arrays are device pointers of length n.  A point whose pixel or
+ * interval index is out of range yields NaN outputs.  Asynchronous. */
+int lift_proj_epi(lift_handle h, const int *pix, const int *interval,
+                  const float *y0, const float *h0, float *y, float *hout,
+                  int n);
+
+/* lift_envelope: rho_i^**(t[j]) at n points (device arrays; t[j] is clamped
+ * into Gamma_i): the convexified pieces that the relaxation uses.  Out-of-
+ * range indices yield NaN. */
+int lift_envelope(lift_handle h, const int *pix, const int *interval,
+                  const float *t, float *out, int n);
+
+const char *lift_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIFT_H */

@@ -1,0 +1,61 @@
+// Internal parameter block of the solver kernels (passed by value) and the
+// host-side launchers.  Not part of the public ABI (include/lift.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+// Largest k handled by the per-pixel work arrays (matches LIFT_MAX_K).
+#define LIFT_MAXK_DEV 64
+
+namespace lift {
+
+struct LiftParams {
+    int H, W, k, N;          // image size, intervals, pixels
+    int kind;                // 0 quadratic, 1 truncated quadratic, 2 PL
+    int ppb;                 // pixels per 256-thread block in the step kernels
+    float inv_k;             // 1/k, for the exact thread -> (pixel, interval) split
+    float delta;             // Delta = gamma_{i+1} - gamma_i (equidistant labels)
+    float gmin;              // gamma_1
+    float lam, alpha, nu;    // TV weight, data-term parameters
+    float wtrunc;            // sqrt(nu/alpha): half-width of the parabola
+    float tau_u, sigma_q, sigma_p;
+    const float4 *icst;      // per interval {gamma_i, tau_s_i, sigma_vz_i, lambda*Delta}
+    const float *f;          // [N] image (quadratic kinds)
+    const float *rhat;       // [N][nb] convexified PL values at the breakpoints
+    const float *cost;       // [N][ns] raw samples (PL)
+    const float *bpos;       // [nb] breakpoint positions (PL)
+    const int *bstart;       // [k+1] first breakpoint of each interval (PL)
+    int nb, ns;              // breakpoints, samples (PL)
+    float smin, sh;          // sample j sits at smin + j*sh (PL)
+};
+
+// Device state of one problem instance (all float32, see include/lift.h).
+struct LiftState {
+    float2 *x;      // [N][k] {u, s}
+    float2 *xbar;   // [N][k] {ubar, sbar}
+    float4 *y;      // [N][k] {v, z, px, py}
+    float *q;       // [N]
+};
+
+constexpr int kStepThreads = 256;
+
+// pdhg_step.cu
+cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+
+// setup_reduce.cu
+cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);
+// Writes per-block partial sums {P_hat, D, E_nc} to partial[nblocks] and the
+// final sums to out[3]; nblocks = energy_blocks(P).
+int energy_blocks(const LiftParams &P);
+cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *partial,
+                          double *out, cudaStream_t st);
+cudaError_t launch_unlift(const LiftParams &P, const float2 *x, float *out, cudaStream_t st);
+cudaError_t launch_proj_epi(const LiftParams &P, const int *pix, const int *interval,
+                            const float *y0, const float *h0, float *y, float *h, int n,
+                            cudaStream_t st);
+cudaError_t launch_envelope(const LiftParams &P, const int *pix, const int *interval,
+                            const float *t, float *out, int n, cudaStream_t st);
+
+}  // namespace lift

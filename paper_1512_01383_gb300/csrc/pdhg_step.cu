@@ -1,0 +1,158 @@
+// The two fused half-steps of the preconditioned primal-dual iteration on the
+// lifted saddle-point problem (arXiv 1512.01383, Sec. 4,
+// eq. discrete_saddle_point_final with the z-splitting of
+// eq. equality_constr_data and its multiplier s):
+//
+//   dual step   (from the extrapolated primal ubar, sbar)
+//     p_i  <- Proj_{|.| <= lambda Delta}(p_i + sigma_p grad ubar_i)        (Prop. 5)
+//     v_l  <- v_l + sigma_l (ubar_l + Delta sum_{j>l} sbar_j - gamma_l sbar_l)
+//     z_i  <- z_i + sigma_i sbar_i
+//     q    <- q - sigma_q (1 + Delta sum_i sbar_i)
+//     (v_i, z_i) <- Delta Proj_{epi rho_i^*}((v_i, z_i) / Delta)           (Fig. 7)
+//   primal step
+//     u_l  <- clamp(u_l - tau_u (v_l - div p_l), 0, 1)
+//     s_i  <- s_i - tau_i (z_i - Delta q + Delta sum_{l<i} v_l - gamma_i v_i)
+//     ubar <- 2 u_new - u,  sbar <- 2 s_new - s
+//
+// Memory: label-innermost records, primal float2 {u,s}, extrapolated primal
+// float2 {ubar,sbar}, dual float4 {v,z,px,py}, q one float per pixel.  One
+// thread owns one (pixel, interval) record, so every warp moves one
+// contiguous, fully coalesced run of 8- or 16-byte records.  A block of 256
+// threads holds floor(256/k) whole pixels; the per-pixel sums over the k
+// intervals (the coupling of v, s and q through the operator of Sec. 4) run
+// through shared memory.  Halo values (ubar at x+1 and y+1 in the dual step,
+// p at x-1 and y-1 in the primal step) are re-read from L1/L2; the
+// algorithmic DRAM traffic is (20k + 3) floats per pixel and iteration.
+#include "lift_device.cuh"
+#include "lift_params.h"
+
+namespace lift {
+
+__device__ __forceinline__ void split_thread(const LiftParams &P, int tid, int &lp, int &i)
+{
+    // (tid + 0.5) / k is at least 0.5/k away from an integer; the float
+    // product is exact to far better than that for tid < 256, k <= 64
+    lp = __float2int_rz((static_cast<float>(tid) + 0.5f) * P.inv_k);
+    i = tid - lp * P.k;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kStepThreads)
+dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
+                 float *__restrict__ q)
+{
+    __shared__ float sb[kStepThreads];
+    const int tid = threadIdx.x;
+    int lp, i;
+    split_thread(P, tid, lp, i);
+    const int pix = blockIdx.x * P.ppb + lp;
+    const bool active = lp < P.ppb && pix < P.N;
+    const size_t o = static_cast<size_t>(pix) * P.k + i;
+
+    float2 xb = make_float2(0.0f, 0.0f);
+    float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (active) {
+        xb = xbar[o];
+        d = y[o];
+    }
+    sb[tid] = xb.y;
+    __syncthreads();
+    if (!active) return;
+
+    const int row = pix / P.W;
+    const int col = pix - row * P.W;
+    const float4 ic = __ldg(P.icst + i);      // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+
+    // TV dual: forward differences (Neumann), ascent, l2-ball projection
+    const float gx = col + 1 < P.W ? xbar[o + P.k].x - xb.x : 0.0f;
+    const float gy = row + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
+    float px = d.z + P.sigma_p * gx;
+    float py = d.w + P.sigma_p * gy;
+    const float nrm = sqrtf(px * px + py * py);
+    if (nrm > ic.w) {
+        const float sc = nrm > 0.0f ? ic.w / nrm : 0.0f;
+        px *= sc;
+        py *= sc;
+    }
+
+    // data duals: suffix sum of sbar over the pixel's later intervals
+    const int base = lp * P.k;
+    float tail = 0.0f;
+    for (int j = i + 1; j < P.k; ++j) tail += sb[base + j];
+    float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
+    float z = d.y + ic.z * xb.y;
+    if (i == 0) q[pix] -= P.sigma_q * (1.0f + P.delta * (xb.y + tail));
+
+    // (v, z) onto Delta * epi(rho_i^*)
+    const float id = 1.0f / P.delta;
+    float yo, ho;
+    piece_project<KIND>(P, pix, i, ic.x, v * id, z * id, yo, ho);
+    v = P.delta * yo;
+    z = P.delta * ho;
+
+    y[o] = make_float4(v, z, px, py);
+}
+
+__global__ void __launch_bounds__(kStepThreads)
+primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
+                   const float4 *__restrict__ y, const float *__restrict__ q)
+{
+    __shared__ float sv[kStepThreads];
+    const int tid = threadIdx.x;
+    int lp, i;
+    split_thread(P, tid, lp, i);
+    const int pix = blockIdx.x * P.ppb + lp;
+    const bool active = lp < P.ppb && pix < P.N;
+    const size_t o = static_cast<size_t>(pix) * P.k + i;
+
+    float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (active) d = y[o];
+    sv[tid] = d.x;
+    __syncthreads();
+    if (!active) return;
+
+    const int row = pix / P.W;
+    const int col = pix - row * P.W;
+    const float4 ic = __ldg(P.icst + i);
+    const float2 xo = x[o];
+    const float qq = q[pix];
+
+    // div p = -grad^T p (Neumann forward differences)
+    float dv = 0.0f;
+    if (col + 1 < P.W) dv += d.z;
+    if (col > 0) dv -= y[o - P.k].z;
+    if (row + 1 < P.H) dv += d.w;
+    if (row > 0) dv -= y[o - static_cast<size_t>(P.W) * P.k].w;
+
+    const int base = lp * P.k;
+    float head = 0.0f;
+    for (int l = 0; l < i; ++l) head += sv[base + l];
+
+    const float un = fminf(fmaxf(xo.x - P.tau_u * (d.x - dv), 0.0f), 1.0f);
+    const float sn = xo.y - ic.y * (d.y - P.delta * qq + P.delta * head - ic.x * d.x);
+    x[o] = make_float2(un, sn);
+    xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
+}
+
+static inline int step_blocks(const LiftParams &P)
+{
+    return (P.N + P.ppb - 1) / P.ppb;
+}
+
+cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+{
+    const int nb = step_blocks(P);
+    if (P.kind == 2)
+        dual_step_kernel<2><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+    else
+        dual_step_kernel<0><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+{
+    primal_step_kernel<<<step_blocks(P), kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q);
+    return cudaGetLastError();
+}
+
+}  // namespace lift

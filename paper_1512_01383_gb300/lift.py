@@ -1,0 +1,303 @@
+"""Thin ctypes binding of ``liblift_gb300.so`` (C ABI in ``include/lift.h``).
+
+The functions below carry the names of the C entry points and only marshal
+arguments; every step of the solver runs in the library's CUDA kernels.
+Device buffers may be passed as ``torch`` CUDA tensors (their data pointers
+are used) and host buffers as numpy arrays.  There is no CPU fallback: if the
+library is missing, loading fails with an error naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED = 0, 1, 2
+LIFT_OK, LIFT_ERR_SPEC, LIFT_ERR_OOM, LIFT_ERR_CUDA = 0, 1, 2, 3
+LIFT_ERR_NAN, LIFT_ERR_NOT_CONVERGED, LIFT_ERR_ARG = 4, 5, 6
+LIFT_MAX_K = 64
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblift_gb300.so")
+
+EXPORTED = (
+    "lift_create", "lift_destroy", "lift_set_data", "lift_reset", "lift_iterate", "lift_solve",
+    "lift_dual_step", "lift_primal_step",
+    "lift_energy", "lift_gap", "lift_unlift", "lift_state_bytes", "lift_get_state",
+    "lift_set_state", "lift_proj_epi", "lift_envelope", "lift_strerror",
+)
+
+
+class lift_spec(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("H", C.c_int), ("W", C.c_int), ("L", C.c_int),
+        ("gamma_min", C.c_double), ("gamma_max", C.c_double), ("lambda_", C.c_double),
+        ("alpha", C.c_double), ("nu", C.c_double),
+        ("f", C.c_void_p), ("cost", C.c_void_p), ("n_samples", C.c_int),
+        ("sample_min", C.c_double), ("sample_max", C.c_double),
+        ("data_on_host", C.c_int), ("check_every", C.c_int),
+    ]
+
+
+class LiftError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    sig = {
+        "lift_create": (C.c_int, [C.POINTER(lift_spec), vp, C.POINTER(vp)]),
+        "lift_destroy": (None, [vp]),
+        "lift_set_data": (C.c_int, [vp, vp, C.c_int]),
+        "lift_reset": (C.c_int, [vp]),
+        "lift_iterate": (C.c_int, [vp, C.c_int]),
+        "lift_solve": (C.c_int, [vp, C.c_int, C.c_double, ip]),
+        "lift_dual_step": (C.c_int, [vp]),
+        "lift_primal_step": (C.c_int, [vp]),
+        "lift_energy": (C.c_int, [vp, dp, dp, dp]),
+        "lift_gap": (C.c_int, [vp, dp]),
+        "lift_unlift": (C.c_int, [vp, vp, C.c_int]),
+        "lift_state_bytes": (C.c_size_t, [vp]),
+        "lift_get_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
+        "lift_set_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
+        "lift_proj_epi": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, C.c_int]),
+        "lift_envelope": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+        "lift_strerror": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().lift_strerror(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != LIFT_OK:
+        raise LiftError(rc, where)
+
+
+def _ptr(a) -> tuple[int, int]:
+    """(address, on_host) of a torch tensor or numpy array."""
+    if a is None:
+        return 0, 1
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, 1
+    # torch.Tensor
+    assert a.is_contiguous()
+    return a.data_ptr(), 0 if a.is_cuda else 1
+
+
+def current_stream() -> int:
+    """cudaStream_t of torch's current stream (0 if torch is unavailable)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# One function per C entry point.
+# ---------------------------------------------------------------------------
+def lift_create(spec: lift_spec, stream: int | None = None) -> int:
+    h = C.c_void_p()
+    s = current_stream() if stream is None else stream
+    _check(load().lift_create(C.byref(spec), C.c_void_p(s), C.byref(h)), "lift_create")
+    return h.value
+
+
+def lift_destroy(h: int) -> None:
+    load().lift_destroy(C.c_void_p(h))
+
+
+def lift_set_data(h: int, data) -> None:
+    p, on_host = _ptr(data)
+    _check(load().lift_set_data(C.c_void_p(h), C.c_void_p(p), on_host), "lift_set_data")
+
+
+def lift_reset(h: int) -> None:
+    _check(load().lift_reset(C.c_void_p(h)), "lift_reset")
+
+
+def lift_iterate(h: int, iters: int) -> None:
+    _check(load().lift_iterate(C.c_void_p(h), iters), "lift_iterate")
+
+
+def lift_dual_step(h: int) -> None:
+    _check(load().lift_dual_step(C.c_void_p(h)), "lift_dual_step")
+
+
+def lift_primal_step(h: int) -> None:
+    _check(load().lift_primal_step(C.c_void_p(h)), "lift_primal_step")
+
+
+def lift_solve(h: int, max_iters: int, rel_gap_tol: float) -> tuple[int, int]:
+    """Returns (status code, iterations done); NOT_CONVERGED is not raised."""
+    n = C.c_int()
+    rc = load().lift_solve(C.c_void_p(h), max_iters, rel_gap_tol, C.byref(n))
+    if rc not in (LIFT_OK, LIFT_ERR_NOT_CONVERGED):
+        raise LiftError(rc, "lift_solve")
+    return rc, n.value
+
+
+def lift_energy(h: int) -> tuple[float, float, float]:
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(load().lift_energy(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)), "lift_energy")
+    return a.value, b.value, c.value
+
+
+def lift_gap(h: int) -> float:
+    g = C.c_double()
+    _check(load().lift_gap(C.c_void_p(h), C.byref(g)), "lift_gap")
+    return g.value
+
+
+def lift_unlift(h: int, out) -> None:
+    p, on_host = _ptr(out)
+    _check(load().lift_unlift(C.c_void_p(h), C.c_void_p(p), on_host), "lift_unlift")
+
+
+def lift_state_bytes(h: int) -> int:
+    return load().lift_state_bytes(C.c_void_p(h))
+
+
+def lift_get_state(h: int, dst) -> None:
+    p, on_host = _ptr(dst)
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(load().lift_get_state(C.c_void_p(h), C.c_void_p(p), nbytes, on_host), "lift_get_state")
+
+
+def lift_set_state(h: int, src) -> None:
+    p, on_host = _ptr(src)
+    nbytes = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+    _check(load().lift_set_state(C.c_void_p(h), C.c_void_p(p), nbytes, on_host), "lift_set_state")
+
+
+def lift_proj_epi(h: int, pix, interval, y0, h0, y, hout) -> None:
+    n = int(y0.numel())
+    args = [C.c_void_p(t.data_ptr()) for t in (pix, interval, y0, h0, y, hout)]
+    _check(load().lift_proj_epi(C.c_void_p(h), *args, n), "lift_proj_epi")
+
+
+def lift_envelope(h: int, pix, interval, t, out) -> None:
+    n = int(t.numel())
+    args = [C.c_void_p(a.data_ptr()) for a in (pix, interval, t, out)]
+    _check(load().lift_envelope(C.c_void_p(h), *args, n), "lift_envelope")
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper holding a handle and the buffers it was created from.
+# ---------------------------------------------------------------------------
+def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: float,
+              lam: float, alpha: float = 1.0, nu: float = 0.0, f=None, cost=None,
+              sample_min: float = 0.0, sample_max: float = 1.0,
+              check_every: int = 100) -> lift_spec:
+    data = f if kind != LIFT_PL_SAMPLED else cost
+    p, on_host = _ptr(data)
+    n_samples = 0
+    if cost is not None:
+        n_samples = int(cost.shape[-1])
+    return lift_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu,
+                     p if kind != LIFT_PL_SAMPLED else 0, p if kind == LIFT_PL_SAMPLED else 0,
+                     n_samples, sample_min, sample_max, on_host, check_every)
+
+
+class Solver:
+    """A lifted problem on the GPU: ``Solver(kind, H, W, L, ...)``."""
+
+    def __init__(self, kind: int, H: int, W: int, L: int, gamma_min: float = 0.0,
+                 gamma_max: float = 1.0, lam: float = 0.0, alpha: float = 1.0,
+                 nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
+                 sample_max: float = 1.0, check_every: int = 100, stream: int | None = None):
+        self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
+        self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
+                              sample_min, sample_max, check_every)
+        self._keep = (f, cost)
+        self.h = lift_create(self.spec, stream)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lift_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        lift_reset(self.h)
+
+    def set_data(self, data):
+        lift_set_data(self.h, data)
+
+    def iterate(self, n: int):
+        lift_iterate(self.h, n)
+
+    def solve(self, max_iters: int, rel_gap_tol: float):
+        return lift_solve(self.h, max_iters, rel_gap_tol)
+
+    def energy(self):
+        return lift_energy(self.h)
+
+    def gap(self):
+        return lift_gap(self.h)
+
+    def unlift(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.H, self.W), dtype=np.float32)
+        lift_unlift(self.h, out)
+        return out
+
+    def state(self) -> dict:
+        """Host copy of the iterate as numpy arrays (layout of include/lift.h)."""
+        nb = lift_state_bytes(self.h)
+        buf = np.empty(nb, dtype=np.uint8)
+        lift_get_state(self.h, buf)
+        N, k = self.H * self.W, self.k
+        f = buf.view(np.float32)
+        o = 0
+        x = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
+        xb = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
+        y = f[o:o + 4 * N * k].reshape(N, k, 4); o += 4 * N * k
+        q = f[o:o + N]
+        return {"u": x[..., 0], "s": x[..., 1], "ubar": xb[..., 0], "sbar": xb[..., 1],
+                "v": y[..., 0], "z": y[..., 1], "px": y[..., 2], "py": y[..., 3], "q": q}
+
+    def set_state(self, st: dict):
+        N, k = self.H * self.W, self.k
+        x = np.stack([st["u"], st["s"]], -1).astype(np.float32).reshape(-1)
+        xb = np.stack([st["ubar"], st["sbar"]], -1).astype(np.float32).reshape(-1)
+        y = np.stack([st["v"], st["z"], st["px"], st["py"]], -1).astype(np.float32).reshape(-1)
+        q = np.asarray(st["q"], dtype=np.float32).reshape(N)
+        buf = np.ascontiguousarray(np.concatenate([x, xb, y, q]))
+        assert buf.size * 4 == lift_state_bytes(self.h) and N * k > 0
+        lift_set_state(self.h, buf)

@@ -1,0 +1,271 @@
+"""GPU (CUDA, FP32) against the FP64 oracle on identical seeded inputs.
+
+Tolerances: the unlifted image within 1e-4 max-abs after normalising by the
+label range, energies within 1e-5 relative, after a fixed iteration count;
+single projections and envelopes within a few FP32 ulps of the point's scale.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from _cases import case, crop, gpu_solver, oracle_problem, oracle_run
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-4       # unlifted image, normalised by (gamma_max - gamma_min)
+E_TOL = 1e-5       # energies, relative
+
+
+def _require_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+# ---------------------------------------------------------------------------
+# Single projections and envelopes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,L", [(0, 4), (1, 5), (1, 3), (2, 6)])
+def test_projection_matches_oracle(kind, L):
+    _require_gpu()
+    c = case(kind, 6, 7, L, 101 + kind)
+    P = oracle_problem(c)
+    rng = np.random.default_rng(5)
+    n = 3000
+    pix = rng.integers(0, P.N, n).astype(np.int32)
+    itv = rng.integers(0, P.k, n).astype(np.int32)
+    scale = (c.get("alpha", 1.0) + 1.0) * (c["gamma_max"] - c["gamma_min"])
+    y0 = rng.uniform(-3 * scale, 3 * scale, n).astype(np.float32)
+    h0 = np.empty(n, np.float32)
+    for j in range(n):
+        phi = O.conj(P, int(pix[j]), int(itv[j]), float(y0[j]))[0]
+        h0[j] = phi + rng.uniform(-4 * scale, 0.5 * scale)
+    with gpu_solver(c) as s:
+        t = lambda a: torch.from_numpy(a).cuda()
+        yo, ho = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+        from paper_1512_01383_gb300 import lift as G
+        G.lift_proj_epi(s.h, t(pix), t(itv), t(y0), t(h0), yo, ho)
+        torch.cuda.synchronize()
+        yo, ho = yo.cpu().numpy(), ho.cpu().numpy()
+    for j in range(n):
+        ry, rh = O.proj_epi(P, int(pix[j]), int(itv[j]), float(y0[j]), float(h0[j]))
+        mag = 1.0 + abs(y0[j]) + abs(h0[j])
+        assert abs(yo[j] - ry) <= 2e-5 * mag, (j, yo[j], ry)
+        assert abs(ho[j] - rh) <= 2e-5 * mag, (j, ho[j], rh)
+
+
+@pytest.mark.parametrize("kind,L", [(0, 4), (1, 5), (1, 2), (2, 6)])
+def test_envelope_matches_oracle(kind, L):
+    _require_gpu()
+    c = case(kind, 5, 4, L, 201 + kind)
+    P = oracle_problem(c)
+    lab = O.labels(c["L"], c["gamma_min"], c["gamma_max"])
+    rng = np.random.default_rng(7)
+    n = 2000
+    pix = rng.integers(0, P.N, n).astype(np.int32)
+    itv = rng.integers(0, P.k, n).astype(np.int32)
+    tt = (lab[itv] + rng.uniform(0, 1, n) * (lab[itv + 1] - lab[itv])).astype(np.float32)
+    with gpu_solver(c) as s:
+        from paper_1512_01383_gb300 import lift as G
+        t = lambda a: torch.from_numpy(a).cuda()
+        out = torch.empty(n, device="cuda")
+        G.lift_envelope(s.h, t(pix), t(itv), t(tt), out)
+        got = out.cpu().numpy()
+    want = np.array([O.biconj(P, int(pix[j]), int(itv[j]), float(tt[j])) for j in range(n)])
+    scale = 1.0 + np.abs(want)
+    assert np.all(np.abs(got - want) <= 2e-5 * scale * (1 + c.get("alpha", 1.0)))
+
+
+# ---------------------------------------------------------------------------
+# Whole iterations
+# ---------------------------------------------------------------------------
+def _compare_state(st, X, P, tol):
+    for name in ("u", "s", "v", "z", "px", "py"):
+        a, b = st[name].reshape(P.N, P.k), getattr(X, name)
+        err = np.abs(a - b).max()
+        assert err <= tol * (1.0 + np.abs(b).max()), (name, err)
+    assert np.abs(st["q"] - X.q).max() <= tol * (1.0 + np.abs(X.q).max())
+
+
+PARITY_CASES = [
+    # kind, H, W, L, iters: several 256-thread blocks plus a ragged tail
+    (0, 37, 29, 2, 300),
+    (1, 37, 29, 5, 300),
+    (1, 23, 31, 10, 200),
+    (1, 19, 17, 20, 120),
+    (2, 21, 19, 5, 150),
+    (2, 13, 11, 17, 80),
+]
+
+
+@pytest.mark.parametrize("kind,H,W,L,iters", PARITY_CASES)
+def test_iterations_match_oracle(kind, H, W, L, iters):
+    _require_gpu()
+    c = case(kind, H, W, L, 300 + H + L)
+    P, X = oracle_run(c, iters)
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        st = s.state()
+        Pg, Dg, Eg = s.energy()
+    rng = c["gamma_max"] - c["gamma_min"]
+    ur = O.unlift(P, X.u).reshape(H, W)
+    assert np.abs(ut - ur).max() / rng <= U_TOL
+    _compare_state(st, X, P, 2e-3)
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
+
+
+@pytest.mark.parametrize("kind,L", [(0, 2), (1, 5), (2, 5)])
+def test_energy_kernel_on_oracle_state(kind, L):
+    """The energy reduction alone: load the oracle's iterate (rounded to
+    float32) into the GPU and evaluate both sides on the same state."""
+    _require_gpu()
+    c = case(kind, 33, 27, L, 400 + kind)
+    P, X = oracle_run(c, 60)
+    names = ("u", "s", "ubar", "sbar", "v", "z", "px", "py")
+    for n in names:
+        getattr(X, n)[...] = getattr(X, n).astype(np.float32).astype(np.float64)
+    X.q[...] = X.q.astype(np.float32).astype(np.float64)
+    with gpu_solver(c) as s:
+        s.set_state({n: getattr(X, n) for n in names} | {"q": X.q})
+        Pg, Dg, Eg = s.energy()
+        ug = s.unlift()
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
+    np.testing.assert_allclose(ug.reshape(-1), O.unlift(P, X.u), atol=1e-6 * (c["gamma_max"] + 1))
+
+
+EDGE_CASES = [
+    (1, 1, 1, 5, 50),     # a single pixel
+    (1, 1, 33, 4, 80),    # one row (1-D)
+    (1, 29, 1, 4, 80),    # one column
+    (0, 3, 5, 2, 100),
+    (1, 9, 7, 65, 30),    # k = 64, the largest supported
+    (1, 11, 13, 33, 40),  # k = 32 (a pixel straddles no warp boundary)
+]
+
+
+@pytest.mark.parametrize("kind,H,W,L,iters", EDGE_CASES)
+def test_edge_shapes(kind, H, W, L, iters):
+    _require_gpu()
+    c = case(kind, H, W, L, 500 + H * W + L)
+    P, X = oracle_run(c, iters)
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        Pg, Dg, Eg = s.energy()
+    ur = O.unlift(P, X.u).reshape(H, W)
+    assert np.abs(ut - ur).max() <= U_TOL
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
+
+
+def test_lambda_zero_and_zero_iterations():
+    _require_gpu()
+    c = case(1, 12, 10, 5, 601, lam=0.0)
+    P, X = oracle_run(c, 100)
+    with gpu_solver(c) as s:
+        z = s.unlift()
+        assert np.all(z == 0.0)           # all-zero start: u~ = gamma_1
+        s.iterate(0)
+        s.iterate(100)
+        ut = s.unlift()
+    assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() <= U_TOL
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads: sampled pixels against oracle crops.  After n
+# iterations a pixel depends only on inputs within 2n pixels (each half-step
+# reads one neighbour per axis), so a crop with a margin of 2n+2 around it
+# (clipped at the true image border) reproduces it exactly.
+# ---------------------------------------------------------------------------
+def _sampled_parity(c, iters, samples, seed):
+    H, W = c["H"], c["W"]
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        st = s.state()
+    m = 2 * iters + 2
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0), (H - 1, W - 1), (0, W - 1)] + [
+        (int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(samples)]
+    for (py_, px_) in pts:
+        y0, y1 = max(0, py_ - m), min(H, py_ + m + 1)
+        x0, x1 = max(0, px_ - m), min(W, px_ + m + 1)
+        cc = crop(c, y0, y1, x0, x1)
+        P, X = oracle_run(cc, iters)
+        j = (py_ - y0) * (x1 - x0) + (px_ - x0)
+        ur = O.unlift(P, X.u)[j]
+        rngl = c["gamma_max"] - c["gamma_min"]
+        assert abs(ut[py_, px_] - ur) / rngl <= U_TOL, (py_, px_, ut[py_, px_], ur)
+        g = py_ * W + px_
+        for name in ("u", "s", "v", "z", "px", "py"):
+            a, b = st[name][g], getattr(X, name)[j]
+            assert np.abs(a - b).max() <= 2e-3 * (1 + np.abs(b).max()), (name, a, b)
+
+
+@pytest.mark.parametrize("L", [5, 10, 20])
+def test_full_size_truncated_512(L):
+    _require_gpu()
+    c = case(1, 512, 512, L, 1512013832)
+    _sampled_parity(c, 3, 5, L)
+
+
+@pytest.mark.parametrize("L", [8, 32])
+def test_full_size_stereo_640x480(L):
+    _require_gpu()
+    c = case(2, 480, 640, L, 1512013834, ndisp=65)
+    _sampled_parity(c, 2, 3, L)
+
+
+# ---------------------------------------------------------------------------
+# API behaviour on the GPU
+# ---------------------------------------------------------------------------
+def test_host_inputs_and_state_roundtrip():
+    _require_gpu()
+    c = case(1, 20, 18, 5, 701)
+    with gpu_solver(c, device_inputs=False) as a, gpu_solver(c) as b:
+        a.iterate(40)
+        b.iterate(40)
+        np.testing.assert_array_equal(a.unlift(), b.unlift())
+        st = a.state()
+        b.reset()
+        b.set_state(st)
+        a.iterate(10)
+        b.iterate(10)
+        np.testing.assert_array_equal(a.unlift(), b.unlift())
+        # device output buffer
+        out = torch.empty((20, 18), device="cuda")
+        a.unlift(out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), a.unlift())
+
+
+def test_solve_reaches_gap_and_reports_iterations():
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(0, 24, 24, 2, 801)
+    with gpu_solver(c, check_every=50) as s:
+        rc, n = s.solve(20000, 1e-5)
+        assert rc == G.LIFT_OK and 0 < n < 20000 and n % 50 == 0
+        assert s.gap() <= 1e-5
+    with gpu_solver(c, check_every=10) as s:
+        rc, n = s.solve(20, 1e-12)
+        assert rc == G.LIFT_ERR_NOT_CONVERGED and n == 20
+
+
+def test_nan_input_reports_nan():
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(1, 8, 8, 5, 901)
+    c["f"] = c["f"].copy()
+    c["f"][3, 3] = np.nan
+    with gpu_solver(c) as s:
+        s.iterate(5)
+        with pytest.raises(G.LiftError) as e:
+            s.energy()
+        assert e.value.code == G.LIFT_ERR_NAN
