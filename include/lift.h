@@ -177,6 +177,39 @@ int lift_proj_epi(lift_handle h, const int *pix, const int *interval,
 int lift_envelope(lift_handle h, const int *pix, const int *interval,
                   const float *t, float *out, int n);
 
+/* ------------------------------------------------ allocation-free variant */
+/* lift_energy_noalloc: the energies of lift_energy for a state that the
+ * caller holds, computed without allocating any memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: code whose device memory all belongs to another allocator (a
+ * framework's caching pool, a fixed memory budget), and code that must not
+ * trigger cudaMalloc / cudaFree because those calls can synchronise the whole
+ * device.  It needs no handle (lift_create allocates).
+ *
+ * spec   a LIFT_QUAD or LIFT_TRUNC_QUAD problem with data_on_host = 0:
+ *        spec->f is read on the device during the call.
+ * state  device pointer, 16-byte aligned, to a state image of this problem
+ *        in the layout of lift_get_state (only the primal and dual parts are
+ *        read).
+ * out    device pointer to 3 doubles: {primal_relaxed, dual, e_nonconvex}.
+ * stream cudaStream_t for the two kernels; the call is asynchronous and
+ *        does not synchronise.
+ *
+ * The per-block partial sums go to one fixed array in the library's device
+ * memory (3 doubles per 256 pixels, 96 KB), which every GPU that loads the
+ * library holds until the process exits.  Hence the limit: H*W must not
+ * exceed LIFT_NOALLOC_MAX_PIXELS, else LIFT_ERR_ARG (as for null pointers,
+ * host-resident data and device ordinals >= 64); other invalid specs give
+ * LIFT_ERR_SPEC.  The first call on each device looks up the array's device
+ * address (one-time set-up, done with that device current); make that first
+ * call before any stream capture.  All calls share the array and each call
+ * overwrites every entry it reads, so nothing has to be cleared between
+ * calls; but calls whose kernels overlap on the GPU (different streams
+ * without ordering between them) race on it and return wrong sums. */
+#define LIFT_NOALLOC_MAX_PIXELS (1 << 20)
+int lift_energy_noalloc(const lift_spec *spec, const void *state, double *out,
+                        void *stream);
+
 const char *lift_strerror(int code);
 
 #ifdef __cplusplus

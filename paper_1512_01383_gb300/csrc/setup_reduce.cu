@@ -2,6 +2,9 @@
 // lifted solver (arXiv 1512.01383).
 #include <math.h>
 
+#include <mutex>
+
+#include "../../include/lift.h"
 #include "lift_device.cuh"
 #include "lift_params.h"
 
@@ -319,3 +322,74 @@ cudaError_t launch_envelope(const LiftParams &P, const int *pix, const int *inte
 }
 
 }  // namespace lift
+
+// ---------------------------------------------------------------------------
+// Allocation-free energy evaluation (lift_energy_noalloc in include/lift.h).
+// The per-block partial sums of energy_kernel go to this fixed array instead
+// of a buffer from cudaMalloc.  Host code must not pass the symbol itself to a
+// kernel (on the host it names a stand-in, not device memory): its device
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocBlocks = (LIFT_NOALLOC_MAX_PIXELS + lift::kEnergyThreads - 1) /
+                               lift::kEnergyThreads;
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_scratch_dev[kNoAllocDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) double lift_noalloc_partial[3 * kNoAllocBlocks];
+
+extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, double *out,
+                                   void *stream)
+{
+    if (!spec || !state || !out) return LIFT_ERR_ARG;
+    if (spec->kind != LIFT_QUAD && spec->kind != LIFT_TRUNC_QUAD) return LIFT_ERR_SPEC;
+    if (spec->data_on_host || !spec->f) return LIFT_ERR_ARG;
+    if (spec->H < 1 || spec->W < 1 || spec->L < 2 || spec->L > LIFT_MAX_K + 1) return LIFT_ERR_SPEC;
+    if (!(spec->gamma_max > spec->gamma_min) || !(spec->lambda >= 0.0) || !(spec->alpha > 0.0))
+        return LIFT_ERR_SPEC;
+    if (spec->kind == LIFT_TRUNC_QUAD && !(spec->nu > 0.0)) return LIFT_ERR_SPEC;
+    const long long npix = static_cast<long long>(spec->H) * spec->W;
+    if (npix > LIFT_NOALLOC_MAX_PIXELS) return LIFT_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(state) & 15u) != 0) return LIFT_ERR_ARG;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LIFT_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocDevices) return LIFT_ERR_ARG;
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_scratch_dev[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, lift_noalloc_partial) != cudaSuccess || !p)
+                return LIFT_ERR_CUDA;
+            g_noalloc_scratch_dev[dev] = static_cast<double *>(p);
+        }
+        scratch = g_noalloc_scratch_dev[dev];
+    }
+
+    lift::LiftParams P{};
+    const int k = spec->L - 1;
+    P.H = spec->H; P.W = spec->W; P.k = k; P.N = static_cast<int>(npix);
+    P.kind = spec->kind;
+    P.delta = static_cast<float>((spec->gamma_max - spec->gamma_min) / k);
+    P.gmin = static_cast<float>(spec->gamma_min);
+    P.lam = static_cast<float>(spec->lambda);
+    P.alpha = static_cast<float>(spec->alpha);
+    P.nu = static_cast<float>(spec->nu);
+    P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
+    P.f = spec->f;
+
+    const size_t Nk = static_cast<size_t>(npix) * k;
+    const float2 *x = static_cast<const float2 *>(state);
+    const float4 *y = reinterpret_cast<const float4 *>(static_cast<const char *>(state) +
+                                                        2 * Nk * sizeof(float2));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nb = lift::energy_blocks(P);
+    lift::energy_kernel<0><<<nb, lift::kEnergyThreads, 0, st>>>(P, x, y, scratch);
+    if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;
+    lift::energy_finish_kernel<<<1, lift::kEnergyThreads, 0, st>>>(scratch, nb, out);
+    if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;
+    return LIFT_OK;
+}

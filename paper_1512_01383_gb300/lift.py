@@ -25,6 +25,7 @@ EXPORTED = (
     "lift_dual_step", "lift_primal_step",
     "lift_energy", "lift_gap", "lift_unlift", "lift_state_bytes", "lift_get_state",
     "lift_set_state", "lift_proj_epi", "lift_envelope", "lift_strerror",
+    "lift_energy_noalloc",
 )
 
 
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
         "lift_proj_epi": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, C.c_int]),
         "lift_envelope": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "lift_strerror": (C.c_char_p, [C.c_int]),
+        "lift_energy_noalloc": (C.c_int, [C.POINTER(lift_spec), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,6 +205,15 @@ def lift_envelope(h: int, pix, interval, t, out) -> None:
     n = int(t.numel())
     args = [C.c_void_p(a.data_ptr()) for a in (pix, interval, t, out)]
     _check(load().lift_envelope(C.c_void_p(h), *args, n), "lift_envelope")
+
+
+def lift_energy_noalloc(spec: lift_spec, state, out, stream: int | None = None) -> None:
+    """Energies of a caller-held device state into out[3] (device), with no
+    allocation (see include/lift.h)."""
+    s = current_stream() if stream is None else stream
+    _check(load().lift_energy_noalloc(C.byref(spec), C.c_void_p(state.data_ptr()),
+                                      C.c_void_p(out.data_ptr()), C.c_void_p(s)),
+           "lift_energy_noalloc")
 
 
 # ---------------------------------------------------------------------------
