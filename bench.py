@@ -35,12 +35,16 @@ H = W = 512
 L = 20
 K_INT = L - 1
 ALPHA, NU, LAM = 25.0, 0.1, 0.25
+# primal/dual step balance theta = k^2 (primal steps x theta, dual steps /
+# theta); found by sweeping theta on the truncated-quadratic problem with the
+# oracle (measurement section)
+THETA = float(K_INT * K_INT)
 ITERS_PER_STEP = 100
 SEED = 1512013831
 METRIC = "lifted PDHG Gpix·label·iter/s"
 UNIT = "Gpix*k*iter/s"
-WORKLOAD = ("truncated-quadratic denoising 512x512, L=20 (k=19), alpha=25 nu=0.1 lambda=0.25; "
-            "step = 100 PDHG iterations + FP64 gap check + unlift")
+WORKLOAD = ("truncated-quadratic denoising 512x512, L=20 (k=19), alpha=25 nu=0.1 lambda=0.25, "
+            "step balance theta=k^2; step = 100 PDHG iterations + FP64 gap check + unlift")
 # Algorithmic DRAM bytes per pixel and launch (float32 records):
 #   dual step  : read xbar 8k + dual 16k + f 4 + q 4, write dual 16k + q 4 = 40k + 12
 #   primal step: read primal 8k + dual 16k + q 4, write primal 8k + xbar 8k = 40k + 4
@@ -132,7 +136,8 @@ def cpu_sample(f: np.ndarray, side: int, iters: int):
     """Time the FP64 oracle on a side x side crop of the workload."""
     import oracle as O
     crop = np.ascontiguousarray(f[:side, :side]).astype(np.float64)
-    P = O.Problem(O.TRUNC, side, side, L, 0.0, 1.0, lam=LAM, alpha=ALPHA, nu=NU, f=crop)
+    P = O.Problem(O.TRUNC, side, side, L, 0.0, 1.0, lam=LAM, alpha=ALPHA, nu=NU, f=crop,
+                  theta=THETA)
     X = O.State(P)
     t0 = time.perf_counter()
     O.pdhg(P, X, iters)
@@ -207,7 +212,7 @@ def main():
     fd = torch.from_numpy(f).to(dev)
     stream = torch.cuda.current_stream(dev)
     solver = G.Solver(G.LIFT_TRUNC_QUAD, H, W, L, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
-                      check_every=ITERS_PER_STEP, stream=stream.cuda_stream)
+                      check_every=ITERS_PER_STEP, stream=stream.cuda_stream, step_balance=THETA)
     uout = torch.empty((H, W), device=dev)
     energy_buf = []
 
@@ -281,13 +286,14 @@ def main():
     if not args.no_ttg and rank == 0:
         for Lx in (5, 10, 20):
             with G.Solver(G.LIFT_TRUNC_QUAD, H, W, Lx, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
-                          check_every=250, stream=stream.cuda_stream) as s2:
+                          check_every=100, stream=stream.cuda_stream,
+                          step_balance=float((Lx - 1) ** 2)) as s2:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 rc, n = s2.solve(60000, 1e-5)
                 dt = time.perf_counter() - t0
                 ttg[f"L{Lx}"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
-                                 "rel_gap": s2.gap()}
+                                 "rel_gap": s2.gap(), "theta": float((Lx - 1) ** 2)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -81,6 +81,9 @@ typedef struct lift_spec {
     double sample_max;
     int data_on_host;         /* 1: f / cost are host pointers, else device */
     int check_every;          /* lift_solve: iterations between gap checks  */
+    double step_balance;      /* theta > 0: every primal step x theta, every
+                                 dual step / theta (tau*sigma unchanged);
+                                 <= 0 means 1, the diagonal preconditioner  */
 } lift_spec;
 
 typedef struct lift_ctx *lift_handle;

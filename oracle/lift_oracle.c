@@ -28,7 +28,8 @@
  *   c_i(v) = <1_{i-1}, v> - gamma_i v_i / Delta_i (appendix form, proof of
  *   Prop. 1); lambda is the radius factor of K (|p_i| <= lambda*Delta_i);
  *   Neumann forward differences; primal box u in [0,1]^k; fixed steps
- *   (no adaptive step rule); dual step first from the extrapolated primal,
+ *   (no adaptive step rule) with a constant primal/dual balance theta that
+ *   the caller chooses; dual step first from the extrapolated primal,
  *   then primal step, then extrapolation with theta = 1; all variables start
  *   at zero.
  *
@@ -55,6 +56,7 @@ typedef struct {
     const double *cost;    /* H*W*ns sampled costs, pixel-major (PL)       */
     int ns;                /* number of samples per pixel (PL)             */
     double smin, smax;     /* sample positions smin + j (smax-smin)/(ns-1)  */
+    double theta;          /* primal/dual step balance (<= 0 means 1)      */
 } orc_problem;
 
 /* PDHG state; all arrays caller-allocated, index [pixel*k + i]. */
@@ -280,7 +282,11 @@ void orc_div(int H, int W, int k, const double *px, const double *py,
 /*   z_i : s_i          q : -sum_i Delta_i s_i        p_i : grad u_i         */
 /* The (v_i, z_i) pair is projected jointly, so it shares one step (the      */
 /* smaller of its two rows); both components of p_i share 1/2; the column   */
-/* of u uses the interior count 1 + 4.                                        */
+/* of u uses the interior count 1 + 4.  A balance theta > 0 then multiplies  */
+/* every primal step and divides every dual step: the products tau*sigma,    */
+/* and with them the convergence condition of the preconditioned method,    */
+/* are unchanged; theta is the primal/dual balance that the adaptive step    */
+/* rule cited in Sec. 4 adjusts.                                             */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double tau_u, sigma_q, sigma_p;
@@ -303,6 +309,14 @@ static void make_steps(const orc_problem *P, orc_steps *S)
         double row_v = 1.0 + fabs(gam(P, i)) + (gam(P, k) - gam(P, i + 1));
         double row_z = 1.0;
         S->sigma_vz[i] = 1.0 / (row_v > row_z ? row_v : row_z);
+    }
+    double th = P->theta > 0.0 ? P->theta : 1.0;
+    S->tau_u *= th;
+    S->sigma_q /= th;
+    S->sigma_p /= th;
+    for (int i = 0; i < k; ++i) {
+        S->tau_s[i] *= th;
+        S->sigma_vz[i] /= th;
     }
 }
 

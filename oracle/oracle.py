@@ -31,7 +31,7 @@ class _Problem(C.Structure):
         ("gmin", C.c_double), ("gmax", C.c_double), ("lam", C.c_double),
         ("alpha", C.c_double), ("nu", C.c_double),
         ("f", _dp), ("cost", _dp), ("ns", C.c_int),
-        ("smin", C.c_double), ("smax", C.c_double),
+        ("smin", C.c_double), ("smax", C.c_double), ("theta", C.c_double),
     ]
 
 
@@ -117,6 +117,7 @@ class Problem:
     cost: np.ndarray | None = None
     smin: float = 0.0
     smax: float = 1.0
+    theta: float = 1.0
     _c: _Problem = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -127,7 +128,7 @@ class Problem:
         ns = 0 if self.cost is None else self.cost.shape[1]
         self._c = _Problem(self.kind, self.H, self.W, self.L, self.gmin, self.gmax, self.lam,
                            self.alpha, self.nu, _ptr(self.f), _ptr(self.cost), ns,
-                           self.smin, self.smax)
+                           self.smin, self.smax, self.theta)
 
     @property
     def k(self) -> int:

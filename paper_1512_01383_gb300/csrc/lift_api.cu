@@ -76,6 +76,7 @@ int validate(const lift_spec *s)
     if (!is_finite(s->gamma_min) || !is_finite(s->gamma_max) || !(s->gamma_max > s->gamma_min))
         return LIFT_ERR_SPEC;
     if (!is_finite(s->lambda) || s->lambda < 0.0) return LIFT_ERR_SPEC;
+    if (!is_finite(s->step_balance)) return LIFT_ERR_SPEC;
     if (s->kind == LIFT_QUAD || s->kind == LIFT_TRUNC_QUAD) {
         if (!s->f) return LIFT_ERR_SPEC;
         if (!is_finite(s->alpha) || !(s->alpha > 0.0)) return LIFT_ERR_SPEC;
@@ -161,12 +162,14 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     // step sizes: reciprocal absolute row / column sums of the operator
     const double d = label(spec, 1) - label(spec, 0);
     const double gL = label(spec, k);
+    // primal/dual balance theta: primal steps x theta, dual steps / theta
+    const double th = spec->step_balance > 0.0 ? spec->step_balance : 1.0;
     std::vector<float4> ic(k);
     for (int i = 0; i < k; ++i) {
         const double gi = label(spec, i);
-        const double tau_s = 1.0 / (1.0 + fabs(gi) + (i + 1) * d);
+        const double tau_s = th / (1.0 + fabs(gi) + (i + 1) * d);
         const double row_v = 1.0 + fabs(gi) + (gL - label(spec, i + 1));
-        const double sig = 1.0 / std::max(row_v, 1.0);
+        const double sig = 1.0 / (th * std::max(row_v, 1.0));
         ic[i] = make_float4(static_cast<float>(gi), static_cast<float>(tau_s),
                             static_cast<float>(sig), static_cast<float>(spec->lambda * d));
     }
@@ -175,16 +178,27 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     P.H = h->H; P.W = h->W; P.k = k; P.N = h->N;
     P.kind = spec->kind;
     P.ppb = lift::kStepThreads / k;
+
     P.inv_k = 1.0f / static_cast<float>(k);
     P.delta = static_cast<float>(d);
+    P.inv_delta = static_cast<float>(1.0 / d);
+    {
+        // exact division by W for 0 <= pix < 2^31: with l = ceil(log2 W) and
+        // M = floor(2^(31+l) / W) + 1, floor(pix*M / 2^(31+l)) = floor(pix/W)
+        // because the excess pix*(M - 2^(31+l)/W)/2^(31+l) < 2^-l <= 1/W
+        int l = 0;
+        while ((1LL << l) < h->W) ++l;
+        P.wshift = 31 + l;
+        P.wmul = ((1ULL << P.wshift) / static_cast<unsigned long long>(h->W)) + 1ULL;
+    }
     P.gmin = static_cast<float>(spec->gamma_min);
     P.lam = static_cast<float>(spec->lambda);
     P.alpha = static_cast<float>(spec->alpha);
     P.nu = static_cast<float>(spec->nu);
     P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
-    P.tau_u = 0.2f;
-    P.sigma_q = static_cast<float>(1.0 / (gL - label(spec, 0)));
-    P.sigma_p = 0.5f;
+    P.tau_u = static_cast<float>(0.2 * th);
+    P.sigma_q = static_cast<float>(1.0 / (th * (gL - label(spec, 0))));
+    P.sigma_p = static_cast<float>(0.5 / th);
 
     std::vector<float> bp;
     std::vector<int> bs;

@@ -13,9 +13,12 @@ namespace lift {
 struct LiftParams {
     int H, W, k, N;          // image size, intervals, pixels
     int kind;                // 0 quadratic, 1 truncated quadratic, 2 PL
-    int ppb;                 // pixels per 256-thread block in the step kernels
+    int ppb;                 // pixels per 256-thread tile in the step kernels
     float inv_k;             // 1/k, for the exact thread -> (pixel, interval) split
+    unsigned long long wmul; // row = (pix * wmul) >> wshift, exact for pix < 2^31
+    int wshift;
     float delta;             // Delta = gamma_{i+1} - gamma_i (equidistant labels)
+    float inv_delta;         // 1/Delta
     float gmin;              // gamma_1
     float lam, alpha, nu;    // TV weight, data-term parameters
     float wtrunc;            // sqrt(nu/alpha): half-width of the parabola

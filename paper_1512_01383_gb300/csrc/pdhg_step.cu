@@ -19,10 +19,12 @@
 // thread owns one (pixel, interval) record, so every warp moves one
 // contiguous, fully coalesced run of 8- or 16-byte records.  A block of 256
 // threads holds floor(256/k) whole pixels; the per-pixel sums over the k
-// intervals (the coupling of v, s and q through the operator of Sec. 4) run
-// through shared memory.  Halo values (ubar at x+1 and y+1 in the dual step,
-// p at x-1 and y-1 in the primal step) are re-read from L1/L2; the
-// algorithmic DRAM traffic is (20k + 3) floats per pixel and iteration.
+// intervals (the coupling of v, s and q through the operator of Sec. 4) are
+// segmented scans: warp shuffles inside each warp, one shared-memory carry
+// for the pixels that straddle a warp boundary.  Halo values (ubar at x+1
+// and y+1 in the dual step, p at x-1 and y-1 in the primal step) are re-read
+// from L1/L2; the algorithmic DRAM traffic is (20k + 3) floats per pixel and
+// iteration (+ f).
 #include "lift_device.cuh"
 #include "lift_params.h"
 
@@ -36,12 +38,54 @@ __device__ __forceinline__ void split_thread(const LiftParams &P, int tid, int &
     i = tid - lp * P.k;
 }
 
+__device__ __forceinline__ int pixel_row(const LiftParams &P, int pix)
+{
+    return static_cast<int>((static_cast<unsigned long long>(pix) * P.wmul) >> P.wshift);
+}
+
+// Inclusive prefix sum of `val` over the thread's pixel segment
+// [seg, seg + k) of the block, and the segment's total.  Every thread of the
+// block must call it (it contains a barrier); threads outside any pixel pass
+// val = 0 and a segment of their own.
+struct SegScan {
+    float incl, total;
+};
+
+__device__ __forceinline__ SegScan block_segmented_scan(float val, int seg, int k, int tid,
+                                                        bool active, float *s_in, float *s_last)
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wbase = warp << 5;
+    const int start = seg > wbase ? seg - wbase : 0;   // first lane of my segment in this warp
+    float x = val;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane - off >= start) x += y;
+    }
+    s_in[tid] = x;
+    if (lane == 31) s_last[warp] = x;
+    __syncthreads();
+    SegScan r{0.0f, 0.0f};
+    if (!active) return r;
+    // segments that began in an earlier warp carry that warp's in-warp total
+    float carry = 0.0f;
+    for (int w = seg >> 5; w < warp; ++w) carry += s_last[w];
+    r.incl = x + carry;
+    const int e = seg + k - 1, ew = e >> 5;
+    float ce = 0.0f;
+    for (int w = seg >> 5; w < ew; ++w) ce += s_last[w];
+    r.total = s_in[e] + ce;
+    return r;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
                  float *__restrict__ q)
 {
-    __shared__ float sb[kStepThreads];
+    __shared__ float s_in[kStepThreads];
+    __shared__ float s_last[kStepThreads / 32];
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
@@ -55,11 +99,10 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
         xb = xbar[o];
         d = y[o];
     }
-    sb[tid] = xb.y;
-    __syncthreads();
+    const SegScan sc = block_segmented_scan(xb.y, lp * P.k, P.k, tid, active, s_in, s_last);
     if (!active) return;
 
-    const int row = pix / P.W;
+    const int row = pixel_row(P, pix);
     const int col = pix - row * P.W;
     const float4 ic = __ldg(P.icst + i);      // {gamma_i, tau_s, sigma_vz, lambda*Delta}
 
@@ -68,25 +111,22 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     const float gy = row + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
     float px = d.z + P.sigma_p * gx;
     float py = d.w + P.sigma_p * gy;
-    const float nrm = sqrtf(px * px + py * py);
-    if (nrm > ic.w) {
-        const float sc = nrm > 0.0f ? ic.w / nrm : 0.0f;
-        px *= sc;
-        py *= sc;
+    const float n2 = px * px + py * py;
+    if (n2 > ic.w * ic.w) {
+        const float sc2 = ic.w * rsqrtf(n2);
+        px *= sc2;
+        py *= sc2;
     }
 
-    // data duals: suffix sum of sbar over the pixel's later intervals
-    const int base = lp * P.k;
-    float tail = 0.0f;
-    for (int j = i + 1; j < P.k; ++j) tail += sb[base + j];
+    // data duals: sum of sbar over the pixel's later intervals = total - inclusive
+    const float tail = sc.total - sc.incl;
     float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
     float z = d.y + ic.z * xb.y;
-    if (i == 0) q[pix] -= P.sigma_q * (1.0f + P.delta * (xb.y + tail));
+    if (i == 0) q[pix] -= P.sigma_q * (1.0f + P.delta * sc.total);
 
     // (v, z) onto Delta * epi(rho_i^*)
-    const float id = 1.0f / P.delta;
     float yo, ho;
-    piece_project<KIND>(P, pix, i, ic.x, v * id, z * id, yo, ho);
+    piece_project<KIND>(P, pix, i, ic.x, v * P.inv_delta, z * P.inv_delta, yo, ho);
     v = P.delta * yo;
     z = P.delta * ho;
 
@@ -97,7 +137,8 @@ __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q)
 {
-    __shared__ float sv[kStepThreads];
+    __shared__ float s_in[kStepThreads];
+    __shared__ float s_last[kStepThreads / 32];
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
@@ -106,15 +147,17 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     const size_t o = static_cast<size_t>(pix) * P.k + i;
 
     float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (active) d = y[o];
-    sv[tid] = d.x;
-    __syncthreads();
+    float2 xo = make_float2(0.0f, 0.0f);
+    if (active) {
+        d = y[o];
+        xo = x[o];
+    }
+    const SegScan sc = block_segmented_scan(d.x, lp * P.k, P.k, tid, active, s_in, s_last);
     if (!active) return;
 
-    const int row = pix / P.W;
+    const int row = pixel_row(P, pix);
     const int col = pix - row * P.W;
     const float4 ic = __ldg(P.icst + i);
-    const float2 xo = x[o];
     const float qq = q[pix];
 
     // div p = -grad^T p (Neumann forward differences)
@@ -124,10 +167,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     if (row + 1 < P.H) dv += d.w;
     if (row > 0) dv -= y[o - static_cast<size_t>(P.W) * P.k].w;
 
-    const int base = lp * P.k;
-    float head = 0.0f;
-    for (int l = 0; l < i; ++l) head += sv[base + l];
-
+    const float head = sc.incl - d.x;             // sum of v over earlier intervals
     const float un = fminf(fmaxf(xo.x - P.tau_u * (d.x - dv), 0.0f), 1.0f);
     const float sn = xo.y - ic.y * (d.y - P.delta * qq + P.delta * head - ic.x * d.x);
     x[o] = make_float2(un, sn);

@@ -36,7 +36,7 @@ class lift_spec(C.Structure):
         ("alpha", C.c_double), ("nu", C.c_double),
         ("f", C.c_void_p), ("cost", C.c_void_p), ("n_samples", C.c_int),
         ("sample_min", C.c_double), ("sample_max", C.c_double),
-        ("data_on_host", C.c_int), ("check_every", C.c_int),
+        ("data_on_host", C.c_int), ("check_every", C.c_int), ("step_balance", C.c_double),
     ]
 
 
@@ -222,7 +222,7 @@ def lift_energy_noalloc(spec: lift_spec, state, out, stream: int | None = None) 
 def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: float,
               lam: float, alpha: float = 1.0, nu: float = 0.0, f=None, cost=None,
               sample_min: float = 0.0, sample_max: float = 1.0,
-              check_every: int = 100) -> lift_spec:
+              check_every: int = 100, step_balance: float = 1.0) -> lift_spec:
     data = f if kind != LIFT_PL_SAMPLED else cost
     p, on_host = _ptr(data)
     n_samples = 0
@@ -230,7 +230,7 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
         n_samples = int(cost.shape[-1])
     return lift_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu,
                      p if kind != LIFT_PL_SAMPLED else 0, p if kind == LIFT_PL_SAMPLED else 0,
-                     n_samples, sample_min, sample_max, on_host, check_every)
+                     n_samples, sample_min, sample_max, on_host, check_every, step_balance)
 
 
 class Solver:
@@ -239,10 +239,11 @@ class Solver:
     def __init__(self, kind: int, H: int, W: int, L: int, gamma_min: float = 0.0,
                  gamma_max: float = 1.0, lam: float = 0.0, alpha: float = 1.0,
                  nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
-                 sample_max: float = 1.0, check_every: int = 100, stream: int | None = None):
+                 sample_max: float = 1.0, check_every: int = 100, stream: int | None = None,
+                 step_balance: float = 1.0):
         self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
         self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
-                              sample_min, sample_max, check_every)
+                              sample_min, sample_max, check_every, step_balance)
         self._keep = (f, cost)
         self.h = lift_create(self.spec, stream)
         self._keep = None

@@ -96,6 +96,28 @@ PARITY_CASES = [
     (2, 21, 19, 5, 150),
     (2, 13, 11, 17, 80),
 ]
+BALANCED_CASES = [
+    # the same with the primal/dual balance of the time-to-gap runs
+    (1, 37, 29, 5, 300, 16.0),
+    (1, 19, 17, 20, 120, 361.0),
+    (0, 25, 23, 2, 200, 0.3),
+]
+
+
+@pytest.mark.parametrize("kind,H,W,L,iters,theta", BALANCED_CASES)
+def test_balanced_steps_match_oracle(kind, H, W, L, iters, theta):
+    _require_gpu()
+    c = case(kind, H, W, L, 350 + H + L, theta=theta)
+    P, X = oracle_run(c, iters)
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        Pg, Dg, Eg = s.energy()
+    ur = O.unlift(P, X.u).reshape(H, W)
+    assert np.abs(ut - ur).max() <= U_TOL
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
 
 
 @pytest.mark.parametrize("kind,H,W,L,iters", PARITY_CASES)

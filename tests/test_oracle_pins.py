@@ -320,6 +320,35 @@ def test_steps_are_reciprocal_abs_sums():
     assert st["sigma_p"] == 0.5
 
 
+def test_step_balance_keeps_step_products():
+    """theta multiplies the primal steps and divides the dual ones, so every
+    product tau*sigma (and the convergence condition) is unchanged."""
+    base = O.Problem(O.TRUNC, 1, 1, 7, -0.3, 1.4, f=np.zeros(1), alpha=1, nu=1)
+    for th in (0.25, 1.0, 49.0):
+        P = O.Problem(O.TRUNC, 1, 1, 7, -0.3, 1.4, f=np.zeros(1), alpha=1, nu=1, theta=th)
+        a, b = O.steps(base), O.steps(P)
+        np.testing.assert_allclose(b["tau_s"], th * a["tau_s"], rtol=1e-15)
+        np.testing.assert_allclose(b["sigma_vz"], a["sigma_vz"] / th, rtol=1e-15)
+        assert b["tau_u"] == pytest.approx(th * a["tau_u"])
+        assert b["sigma_q"] == pytest.approx(a["sigma_q"] / th)
+        assert b["sigma_p"] == pytest.approx(a["sigma_p"] / th)
+
+
+@pytest.mark.parametrize("theta", [0.3, 4.0])
+def test_step_balance_reaches_the_same_optimum(theta):
+    """Any balance converges to the same optimum: L = 2 ROF against the
+    independent direct solver."""
+    f = synth.gaussian_blobs(9, 8, 45)
+    u_dir, gap = O.rof_direct(f, 1.0, 0.2, 0.0, 1.0, 100000)
+    Er = O.rof_energy(u_dir, f, 1.0, 0.2)
+    P = O.Problem(O.QUAD, 9, 8, 2, 0.0, 1.0, lam=0.2, alpha=1.0, f=f, theta=theta)
+    X = O.State(P)
+    O.pdhg(P, X, 6000)
+    Ph, D, _ = O.energy(P, X)
+    assert D <= Er + 1e-12 and abs(Ph - Er) < 1e-8 * Er and abs(D - Er) < 1e-8 * Er
+    assert np.abs(O.unlift(P, X.u).reshape(9, 8) - u_dir).max() < 2e-5
+
+
 @pytest.mark.parametrize("alpha", [1.0, 2.5])
 def test_L2_equals_direct_rof(alpha):
     """Prop. 3: with L = 2 the relaxation is the unlifted problem; for the
