@@ -148,6 +148,62 @@ def cpu_sample(f: np.ndarray, side: int, iters: int):
     return units / dt / 1e9, dt
 
 
+def run_batch(G, torch, stream, dev, n=64, smin=128, smax=1024, iters=100, reps=3):
+    """Serving-style batch: n truncated-quadratic instances, side ~ U{smin..smax},
+    L ~ U{4,8,16,32}, theta = k^2 each: one graph launch per 100 iterations
+    over all instances (tile width autotuned) against a loop of single-handle
+    solves of the same instances."""
+    from paper_1512_01383_gb300 import synth
+    inst = synth.batch_instances(n, synth.BASE_SEED + 2, smin, smax)
+    fs = [torch.from_numpy(synth.as_f32(synth.voronoi_ramps(sd, sd, synth.BASE_SEED + 2 + 1000 * j)[0])).to(dev)
+          for j, (sd, Lj) in enumerate(inst)]
+    specs = [G.make_spec(G.LIFT_TRUNC_QUAD, sd, sd, Lj, 0.0, 1.0, LAM, ALPHA, NU, f=f,
+                         check_every=iters, step_balance=float((Lj - 1) ** 2))
+             for (sd, Lj), f in zip(inst, fs)]
+    units = sum(sd * sd * (Lj - 1) for sd, Lj in inst) * iters
+    # graph capture needs a stream other than the legacy default stream: run
+    # the whole section (events included) on a stream of its own
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    b = G.lift_create_batch(specs, stream.cuda_stream)
+    try:
+        threads = G.lift_batch_autotune(b, 3)
+        G.lift_batch_iterate(b, iters)           # capture + warm-up
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            G.lift_batch_iterate(b, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / reps
+    finally:
+        G.lift_batch_destroy(b)
+    # the same instances as a loop of single solves
+    hs = [G.Solver(G.LIFT_TRUNC_QUAD, sd, sd, Lj, 0.0, 1.0, LAM, ALPHA, NU, f=f,
+                   stream=stream.cuda_stream, step_balance=float((Lj - 1) ** 2))
+          for (sd, Lj), f in zip(inst, fs)]
+    for h in hs:
+        h.iterate(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for h in hs:
+            h.iterate(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / reps
+    for h in hs:
+        h.close()
+    return {"instances": n, "side_range": [smin, smax], "pixels": sum(sd * sd for sd, _ in inst),
+            "pix_k": sum(sd * sd * (Lj - 1) for sd, Lj in inst), "iters_per_launch": iters,
+            "tile_threads": threads,
+            "value": units / (ms_batch * 1e-3) / 1e9, "unit": UNIT,
+            "loop_of_single_solves": units / (ms_loop * 1e-3) / 1e9,
+            "speedup_vs_loop": ms_loop / ms_batch,
+            "ms_per_100_iters": ms_batch}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -184,6 +240,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap runs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -295,6 +352,11 @@ def main():
                 ttg[f"L{Lx}"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
                                  "rel_gap": s2.gap(), "theta": float((Lx - 1) ** 2)}
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = run_batch(G, torch, stream, dev)
+        batch["small_instances"] = run_batch(G, torch, stream, dev, n=256, smin=32, smax=128)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side, iters = 96, 50
@@ -325,6 +387,7 @@ def main():
             "gpu_launches": args.steps * (2 * ITERS_PER_STEP + 3),
             "clocks": clk.summary(),
             "time_to_gap_1e-5": ttg or None,
+            "batch": batch,
             "final_energy": {"primal": energy_buf[-1][0], "dual": energy_buf[-1][1],
                              "nonconvex": energy_buf[-1][2]},
         }

@@ -180,6 +180,58 @@ int lift_proj_epi(lift_handle h, const int *pix, const int *interval,
 int lift_envelope(lift_handle h, const int *pix, const int *interval,
                   const float *t, float *out, int n);
 
+/* --------------------------------------------------------------- batches */
+/* A batch solves many independent problems (each its own size, label count
+ * and data; one data-term kind, LIFT_QUAD or LIFT_TRUNC_QUAD) together: each
+ * half-step is one launch over the tiles of every instance, and each
+ * check_every iterations (of specs[0]) are replayed as one CUDA graph.
+ * Instances found converged by lift_batch_solve stop iterating (their blocks
+ * exit at once) while the others continue.  The iteration of each instance is
+ * the same map as a single handle's (the same kernels on the same tiles). */
+typedef struct lift_batch_ctx *lift_batch;
+
+/* lift_create_batch: n >= 1 specs (each validated as by lift_create; PL and
+ * mixed kinds give LIFT_ERR_SPEC).  stream: cudaStream_t for all work of the
+ * batch; NULL makes the batch create (and later destroy) its own
+ * non-blocking stream, because graph capture cannot use the legacy default
+ * stream; work on that private stream is not ordered with the caller's
+ * legacy-default-stream work, so such callers synchronise the device before
+ * reading results.  All state lives in one device allocation owned by the
+ * batch. */
+int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *out);
+void lift_batch_destroy(lift_batch b);
+int lift_batch_size(lift_batch b);
+
+/* lift_batch_reset: zero every iterate; mark every instance live. */
+int lift_batch_reset(lift_batch b);
+
+/* lift_batch_iterate: `iters` iterations of every live instance
+ * (asynchronous; whole check intervals run as one graph launch). */
+int lift_batch_iterate(lift_batch b, int iters);
+
+/* lift_batch_solve: iterate in check intervals until every instance's
+ * relative gap (as lift_gap) is <= rel_gap_tol or max_iters is reached.
+ * iters_done (n ints, may be NULL): iterations each instance ran;
+ * n_converged (may be NULL).  LIFT_ERR_NOT_CONVERGED if some did not. */
+int lift_batch_solve(lift_batch b, int max_iters, double rel_gap_tol, int *iters_done,
+                     int *n_converged);
+
+/* lift_batch_energy: out[3*i .. 3*i+2] = {primal_relaxed, dual, e_nonconvex}
+ * of instance i (as lift_energy), host array of 3n doubles.  Synchronises. */
+int lift_batch_energy(lift_batch b, double *out);
+
+/* lift_batch_unlift: unlifted image of instance i into out (H_i*W_i floats,
+ * device or host per on_host). */
+int lift_batch_unlift(lift_batch b, int i, float *out, int on_host);
+
+/* lift_batch_get_state: state image of instance i (layout of lift_get_state). */
+int lift_batch_get_state(lift_batch b, int i, void *dst, size_t bytes, int on_host);
+
+/* lift_batch_autotune: time `iters` iterations for tile widths of 128, 256
+ * and 512 threads on this batch and keep the fastest (*threads_chosen, may
+ * be NULL).  Resets every iterate to zero. */
+int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen);
+
 /* ------------------------------------------------ allocation-free variant */
 /* lift_energy_noalloc: the energies of lift_energy for a state that the
  * caller holds, computed without allocating any memory.  The paper has no

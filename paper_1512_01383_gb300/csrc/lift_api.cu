@@ -126,6 +126,50 @@ int pl_breakpoints(const lift_spec *s, std::vector<float> &pos, std::vector<int>
     return LIFT_OK;
 }
 
+// Kernel parameters of one problem (everything but the device pointers):
+// step sizes from the reciprocal absolute row / column sums of the operator,
+// scaled by the primal/dual balance theta; per-interval constants in ic.
+void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<float4> &ic)
+{
+    const int k = spec->L - 1;
+    const double d = label(spec, 1) - label(spec, 0);
+    const double gL = label(spec, k);
+    const double th = spec->step_balance > 0.0 ? spec->step_balance : 1.0;
+    ic.assign(k, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    for (int i = 0; i < k; ++i) {
+        const double gi = label(spec, i);
+        const double tau_s = th / (1.0 + fabs(gi) + (i + 1) * d);
+        const double row_v = 1.0 + fabs(gi) + (gL - label(spec, i + 1));
+        const double sig = 1.0 / (th * std::max(row_v, 1.0));
+        ic[i] = make_float4(static_cast<float>(gi), static_cast<float>(tau_s),
+                            static_cast<float>(sig), static_cast<float>(spec->lambda * d));
+    }
+    P = LiftParams{};
+    P.H = spec->H; P.W = spec->W; P.k = k; P.N = spec->H * spec->W;
+    P.kind = spec->kind;
+    P.ppb = threads / k;
+    P.inv_k = 1.0f / static_cast<float>(k);
+    P.delta = static_cast<float>(d);
+    P.inv_delta = static_cast<float>(1.0 / d);
+    {
+        // exact division by W for 0 <= pix < 2^31: with l = ceil(log2 W) and
+        // M = floor(2^(31+l) / W) + 1, floor(pix*M / 2^(31+l)) = floor(pix/W)
+        // because the excess pix*(M - 2^(31+l)/W)/2^(31+l) < 2^-l <= 1/W
+        int l = 0;
+        while ((1LL << l) < spec->W) ++l;
+        P.wshift = 31 + l;
+        P.wmul = ((1ULL << P.wshift) / static_cast<unsigned long long>(spec->W)) + 1ULL;
+    }
+    P.gmin = static_cast<float>(spec->gamma_min);
+    P.lam = static_cast<float>(spec->lambda);
+    P.alpha = static_cast<float>(spec->alpha);
+    P.nu = static_cast<float>(spec->nu);
+    P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
+    P.tau_u = static_cast<float>(0.2 * th);
+    P.sigma_q = static_cast<float>(1.0 / (th * (gL - label(spec, 0))));
+    P.sigma_p = static_cast<float>(0.5 / th);
+}
+
 int upload_data(lift_handle h, const float *data, int on_host)
 {
     float *dst = h->kind == LIFT_PL_SAMPLED ? h->cost : h->f;
@@ -159,46 +203,9 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     const int k = h->k;
     const size_t N = static_cast<size_t>(h->N), Nk = N * k;
 
-    // step sizes: reciprocal absolute row / column sums of the operator
-    const double d = label(spec, 1) - label(spec, 0);
-    const double gL = label(spec, k);
-    // primal/dual balance theta: primal steps x theta, dual steps / theta
-    const double th = spec->step_balance > 0.0 ? spec->step_balance : 1.0;
-    std::vector<float4> ic(k);
-    for (int i = 0; i < k; ++i) {
-        const double gi = label(spec, i);
-        const double tau_s = th / (1.0 + fabs(gi) + (i + 1) * d);
-        const double row_v = 1.0 + fabs(gi) + (gL - label(spec, i + 1));
-        const double sig = 1.0 / (th * std::max(row_v, 1.0));
-        ic[i] = make_float4(static_cast<float>(gi), static_cast<float>(tau_s),
-                            static_cast<float>(sig), static_cast<float>(spec->lambda * d));
-    }
-
+    std::vector<float4> ic;
     LiftParams &P = h->P;
-    P.H = h->H; P.W = h->W; P.k = k; P.N = h->N;
-    P.kind = spec->kind;
-    P.ppb = lift::kStepThreads / k;
-
-    P.inv_k = 1.0f / static_cast<float>(k);
-    P.delta = static_cast<float>(d);
-    P.inv_delta = static_cast<float>(1.0 / d);
-    {
-        // exact division by W for 0 <= pix < 2^31: with l = ceil(log2 W) and
-        // M = floor(2^(31+l) / W) + 1, floor(pix*M / 2^(31+l)) = floor(pix/W)
-        // because the excess pix*(M - 2^(31+l)/W)/2^(31+l) < 2^-l <= 1/W
-        int l = 0;
-        while ((1LL << l) < h->W) ++l;
-        P.wshift = 31 + l;
-        P.wmul = ((1ULL << P.wshift) / static_cast<unsigned long long>(h->W)) + 1ULL;
-    }
-    P.gmin = static_cast<float>(spec->gamma_min);
-    P.lam = static_cast<float>(spec->lambda);
-    P.alpha = static_cast<float>(spec->alpha);
-    P.nu = static_cast<float>(spec->nu);
-    P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
-    P.tau_u = static_cast<float>(0.2 * th);
-    P.sigma_q = static_cast<float>(1.0 / (th * (gL - label(spec, 0))));
-    P.sigma_p = static_cast<float>(0.5 / th);
+    make_params(spec, lift::kStepThreads, P, ic);
 
     std::vector<float> bp;
     std::vector<int> bs;
@@ -448,6 +455,370 @@ const char *lift_strerror(int code)
     case LIFT_ERR_ARG: return "invalid argument";
     default: return "unknown error code";
     }
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many problem instances solved together (one launch per half-step
+// over all instances' tiles, captured in a CUDA graph per check interval).
+// ===========================================================================
+struct lift_batch_ctx {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n = 0, kind = 0, check_every = 100, threads = lift::kStepThreads;
+    std::vector<LiftParams> P;          // host copies (device pointers filled in)
+    std::vector<LiftState> S;
+    std::vector<int> ntiles;            // per instance, for the current tile width
+    void *arena = nullptr;              // all per-instance device arrays
+    lift::InstDesc *desc = nullptr;     // device [n]
+    int *tile_inst = nullptr;           // device [total tiles]
+    int total_tiles = 0;
+    int *live = nullptr;                // device [n]: 1 = still iterating
+    std::vector<int> live_h;
+    std::vector<long long> iters_h;     // iterations done per instance
+    double *partial = nullptr, *dout = nullptr, *hout = nullptr;
+    float *ubuf = nullptr;              // unlift staging for host output
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_iters = 0;
+};
+
+namespace {
+
+void drop_graph(lift_batch b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_iters = 0;
+}
+
+void free_batch(lift_batch b)
+{
+    if (!b) return;
+    drop_graph(b);
+    void *ptrs[] = {b->arena, b->desc, b->tile_inst, b->live, b->partial, b->dout, b->ubuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (b->hout) cudaFreeHost(b->hout);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// (Re)build the tile list for a tile width of `threads` threads.
+int batch_set_tiles(lift_batch b, int threads)
+{
+    std::vector<lift::InstDesc> d(b->n);
+    std::vector<int> ti;
+    int t0 = 0;
+    for (int j = 0; j < b->n; ++j) {
+        b->P[j].ppb = threads / b->P[j].k;
+        const int nt = (b->P[j].N + b->P[j].ppb - 1) / b->P[j].ppb;
+        b->ntiles[j] = nt;
+        d[j].P = b->P[j];
+        d[j].S = b->S[j];
+        d[j].tile0 = t0;
+        d[j].ntiles = nt;
+        ti.insert(ti.end(), nt, j);
+        t0 += nt;
+    }
+    if (b->tile_inst) cudaFree(b->tile_inst);
+    b->tile_inst = nullptr;
+    int rc = dev_alloc(reinterpret_cast<void **>(&b->tile_inst), ti.size() * sizeof(int));
+    if (rc != LIFT_OK) return rc;
+    LIFT_CK(cudaMemcpyAsync(b->tile_inst, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream));
+    LIFT_CK(cudaMemcpyAsync(b->desc, d.data(), d.size() * sizeof(lift::InstDesc),
+                            cudaMemcpyHostToDevice, b->stream));
+    LIFT_CK(cudaStreamSynchronize(b->stream));   // host vectors die here
+    b->total_tiles = t0;
+    b->threads = threads;
+    drop_graph(b);
+    return LIFT_OK;
+}
+
+int batch_launch(lift_batch b, int iters)
+{
+    for (int it = 0; it < iters; ++it)
+        LIFT_CK(lift::launch_batch_iteration(b->kind, b->threads, b->desc, b->tile_inst, b->live,
+                                             b->total_tiles, b->stream));
+    return LIFT_OK;
+}
+
+int batch_capture(lift_batch b, int iters)
+{
+    drop_graph(b);
+    LIFT_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = batch_launch(b, iters);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != LIFT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return LIFT_ERR_CUDA;
+    }
+    b->graph = g;
+    LIFT_CK(cudaGraphInstantiate(&b->exec, g, 0));
+    b->graph_iters = iters;
+    return LIFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *out)
+{
+    if (!specs || !out || n < 1) return LIFT_ERR_ARG;
+    *out = nullptr;
+    for (int j = 0; j < n; ++j) {
+        const int rc = validate(&specs[j]);
+        if (rc != LIFT_OK) return rc;
+        if (specs[j].kind == LIFT_PL_SAMPLED || specs[j].kind != specs[0].kind) return LIFT_ERR_SPEC;
+    }
+    lift_batch b = new (std::nothrow) lift_batch_ctx();
+    if (!b) return LIFT_ERR_OOM;
+    b->n = n;
+    b->kind = specs[0].kind;
+    b->check_every = specs[0].check_every > 0 ? specs[0].check_every : 100;
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return LIFT_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    b->P.resize(n);
+    b->S.resize(n);
+    b->ntiles.assign(n, 0);
+    b->live_h.assign(n, 1);
+    b->iters_h.assign(n, 0);
+
+    // one arena: per instance x, xbar, y, q, f, icst (256-byte aligned)
+    std::vector<std::vector<float4>> ics(n);
+    std::vector<size_t> off(n * 6);
+    size_t total = 0;
+    auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
+    int max_eblocks = 1;
+    size_t max_n = 1;
+    for (int j = 0; j < n; ++j) {
+        make_params(&specs[j], lift::kStepThreads, b->P[j], ics[j]);
+        const size_t N = static_cast<size_t>(b->P[j].N), Nk = N * b->P[j].k;
+        off[6 * j + 0] = take(Nk * sizeof(float2));
+        off[6 * j + 1] = take(Nk * sizeof(float2));
+        off[6 * j + 2] = take(Nk * sizeof(float4));
+        off[6 * j + 3] = take(N * sizeof(float));
+        off[6 * j + 4] = take(N * sizeof(float));
+        off[6 * j + 5] = take(b->P[j].k * sizeof(float4));
+        max_eblocks = std::max(max_eblocks, lift::energy_blocks(b->P[j]));
+        max_n = std::max(max_n, N);
+    }
+    int rc = dev_alloc(&b->arena, total);
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->desc), n * sizeof(lift::InstDesc));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->live), n * sizeof(int));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->partial), 3 * sizeof(double) * max_eblocks);
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->dout), 3 * sizeof(double) * n);
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->ubuf), max_n * sizeof(float));
+    if (rc == LIFT_OK && cudaMallocHost(reinterpret_cast<void **>(&b->hout), 3 * sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        b->hout = nullptr;
+        rc = LIFT_ERR_OOM;
+    }
+    if (rc != LIFT_OK) { free_batch(b); return rc; }
+    char *base = static_cast<char *>(b->arena);
+    for (int j = 0; j < n; ++j) {
+        LiftState &S = b->S[j];
+        S.x = reinterpret_cast<float2 *>(base + off[6 * j + 0]);
+        S.xbar = reinterpret_cast<float2 *>(base + off[6 * j + 1]);
+        S.y = reinterpret_cast<float4 *>(base + off[6 * j + 2]);
+        S.q = reinterpret_cast<float *>(base + off[6 * j + 3]);
+        float *f = reinterpret_cast<float *>(base + off[6 * j + 4]);
+        float4 *ic = reinterpret_cast<float4 *>(base + off[6 * j + 5]);
+        b->P[j].f = f;
+        b->P[j].icst = ic;
+        const size_t N = static_cast<size_t>(b->P[j].N);
+        if (cudaMemcpyAsync(f, specs[j].f, N * sizeof(float),
+                            specs[j].data_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(ic, ics[j].data(), ics[j].size() * sizeof(float4),
+                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+            free_batch(b);
+            return LIFT_ERR_CUDA;
+        }
+    }
+    rc = batch_set_tiles(b, lift::kStepThreads);   // synchronises (ics die here)
+    if (rc == LIFT_OK) rc = lift_batch_reset(b);
+    if (rc != LIFT_OK) { free_batch(b); return rc; }
+    *out = b;
+    return LIFT_OK;
+}
+
+void lift_batch_destroy(lift_batch b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+}
+
+int lift_batch_size(lift_batch b)
+{
+    return b ? b->n : 0;
+}
+
+int lift_batch_reset(lift_batch b)
+{
+    if (!b) return LIFT_ERR_ARG;
+    for (int j = 0; j < b->n; ++j) {
+        const size_t N = static_cast<size_t>(b->P[j].N), Nk = N * b->P[j].k;
+        LIFT_CK(cudaMemsetAsync(b->S[j].x, 0, Nk * sizeof(float2), b->stream));
+        LIFT_CK(cudaMemsetAsync(b->S[j].xbar, 0, Nk * sizeof(float2), b->stream));
+        LIFT_CK(cudaMemsetAsync(b->S[j].y, 0, Nk * sizeof(float4), b->stream));
+        LIFT_CK(cudaMemsetAsync(b->S[j].q, 0, N * sizeof(float), b->stream));
+    }
+    b->live_h.assign(b->n, 1);
+    b->iters_h.assign(b->n, 0);
+    LIFT_CK(cudaMemcpyAsync(b->live, b->live_h.data(), b->n * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream));
+    LIFT_CK(cudaStreamSynchronize(b->stream));
+    return LIFT_OK;
+}
+
+int lift_batch_iterate(lift_batch b, int iters)
+{
+    if (!b || iters < 0) return LIFT_ERR_ARG;
+    int done = 0;
+    while (iters - done >= b->check_every) {
+        if (!b->exec || b->graph_iters != b->check_every) {
+            const int rc = batch_capture(b, b->check_every);
+            if (rc != LIFT_OK) return rc;
+        }
+        LIFT_CK(cudaGraphLaunch(b->exec, b->stream));
+        done += b->check_every;
+    }
+    const int rc = batch_launch(b, iters - done);
+    if (rc != LIFT_OK) return rc;
+    for (int j = 0; j < b->n; ++j)
+        if (b->live_h[j]) b->iters_h[j] += iters;
+    return LIFT_OK;
+}
+
+int lift_batch_energy(lift_batch b, double *out)
+{
+    if (!b || !out) return LIFT_ERR_ARG;
+    for (int j = 0; j < b->n; ++j)
+        LIFT_CK(lift::launch_energy(b->P[j], b->S[j], b->partial, b->dout + 3 * j, b->stream));
+    LIFT_CK(cudaMemcpyAsync(b->hout, b->dout, 3 * sizeof(double) * b->n, cudaMemcpyDeviceToHost,
+                            b->stream));
+    LIFT_CK(cudaStreamSynchronize(b->stream));
+    memcpy(out, b->hout, 3 * sizeof(double) * b->n);
+    for (int j = 0; j < 3 * b->n; ++j)
+        if (!is_finite(out[j])) return LIFT_ERR_NAN;
+    return LIFT_OK;
+}
+
+int lift_batch_solve(lift_batch b, int max_iters, double rel_gap_tol, int *iters_done,
+                     int *n_converged)
+{
+    if (!b || max_iters < 0) return LIFT_ERR_ARG;
+    std::vector<double> e(3 * b->n);
+    int conv = 0;
+    long long done = 0;
+    while (done < max_iters) {
+        const int chunk = static_cast<int>(std::min<long long>(b->check_every, max_iters - done));
+        int rc = lift_batch_iterate(b, chunk);
+        if (rc != LIFT_OK) return rc;
+        done += chunk;
+        rc = lift_batch_energy(b, e.data());
+        if (rc != LIFT_OK) return rc;
+        conv = 0;
+        bool changed = false;
+        for (int j = 0; j < b->n; ++j) {
+            const double p = e[3 * j], d = e[3 * j + 1];
+            const double g = (p - d) / std::max(std::max(fabs(p), fabs(d)), 1.0);
+            if (b->live_h[j] && g <= rel_gap_tol) { b->live_h[j] = 0; changed = true; }
+            conv += b->live_h[j] ? 0 : 1;
+        }
+        if (changed)
+            LIFT_CK(cudaMemcpyAsync(b->live, b->live_h.data(), b->n * sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream));
+        if (conv == b->n) break;
+    }
+    if (iters_done)
+        for (int j = 0; j < b->n; ++j) iters_done[j] = static_cast<int>(b->iters_h[j]);
+    if (n_converged) *n_converged = conv;
+    return conv == b->n ? LIFT_OK : LIFT_ERR_NOT_CONVERGED;
+}
+
+int lift_batch_unlift(lift_batch b, int i, float *out, int on_host)
+{
+    if (!b || !out || i < 0 || i >= b->n) return LIFT_ERR_ARG;
+    const size_t N = static_cast<size_t>(b->P[i].N);
+    if (!on_host) {
+        LIFT_CK(lift::launch_unlift(b->P[i], b->S[i].x, out, b->stream));
+        return LIFT_OK;
+    }
+    LIFT_CK(lift::launch_unlift(b->P[i], b->S[i].x, b->ubuf, b->stream));
+    LIFT_CK(cudaMemcpyAsync(out, b->ubuf, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    LIFT_CK(cudaStreamSynchronize(b->stream));
+    return LIFT_OK;
+}
+
+int lift_batch_get_state(lift_batch b, int i, void *dst, size_t bytes, int on_host)
+{
+    if (!b || !dst || i < 0 || i >= b->n) return LIFT_ERR_ARG;
+    const size_t N = static_cast<size_t>(b->P[i].N), Nk = N * b->P[i].k;
+    const size_t sizes[4] = {Nk * sizeof(float2), Nk * sizeof(float2), Nk * sizeof(float4),
+                             N * sizeof(float)};
+    if (bytes != sizes[0] + sizes[1] + sizes[2] + sizes[3]) return LIFT_ERR_ARG;
+    const void *parts[4] = {b->S[i].x, b->S[i].xbar, b->S[i].y, b->S[i].q};
+    size_t o = 0;
+    for (int j = 0; j < 4; ++j) {
+        LIFT_CK(cudaMemcpyAsync(static_cast<char *>(dst) + o, parts[j], sizes[j],
+                                on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                b->stream));
+        o += sizes[j];
+    }
+    if (on_host) LIFT_CK(cudaStreamSynchronize(b->stream));
+    return LIFT_OK;
+}
+
+int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen)
+{
+    if (!b || iters < 1) return LIFT_ERR_ARG;
+    const int cand[3] = {128, 256, 512};
+    float best_ms = 0.0f;
+    int best = lift::kStepThreads;
+    cudaEvent_t e0, e1;
+    LIFT_CK(cudaEventCreate(&e0));
+    LIFT_CK(cudaEventCreate(&e1));
+    int rc = LIFT_OK;
+    for (int c = 0; c < 3 && rc == LIFT_OK; ++c) {
+        bool ok = true;
+        for (int j = 0; j < b->n; ++j) ok = ok && cand[c] >= b->P[j].k;
+        if (!ok) continue;
+        rc = batch_set_tiles(b, cand[c]);
+        if (rc == LIFT_OK) rc = lift_batch_reset(b);
+        if (rc == LIFT_OK) rc = batch_launch(b, 2);           // warm-up
+        if (rc != LIFT_OK) break;
+        cudaEventRecord(e0, b->stream);
+        rc = batch_launch(b, iters);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LIFT_ERR_CUDA; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LIFT_OK) return rc;
+    rc = batch_set_tiles(b, best);
+    if (rc == LIFT_OK) rc = lift_batch_reset(b);
+    if (rc == LIFT_OK && threads_chosen) *threads_chosen = best;
+    return rc;
 }
 
 }  // extern "C"

@@ -41,11 +41,22 @@ struct LiftState {
     float *q;       // [N]
 };
 
+// One instance of a batch: its parameters, its state and its first tile in
+// the batch's global tile list.
+struct InstDesc {
+    LiftParams P;
+    LiftState S;
+    int tile0, ntiles;
+};
+
 constexpr int kStepThreads = 256;
 
 // pdhg_step.cu
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+
+cudaError_t launch_batch_iteration(int kind, int threads, const InstDesc *D, const int *tile_inst,
+                                   const int *live, int ntiles, cudaStream_t st);
 
 // setup_reduce.cu
 cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);

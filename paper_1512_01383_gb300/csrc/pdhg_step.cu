@@ -53,6 +53,7 @@ struct SegScan {
 
 __device__ __forceinline__ SegScan block_segmented_scan(float val, int seg, int k, int tid,
                                                         bool active, float *s_in, float *s_last)
+    // s_in: one float per thread; s_last: one float per warp
 {
     const int lane = tid & 31, warp = tid >> 5;
     const int wbase = warp << 5;
@@ -79,17 +80,18 @@ __device__ __forceinline__ SegScan block_segmented_scan(float val, int seg, int 
     return r;
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(kStepThreads)
-dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
-                 float *__restrict__ q)
+// One tile: floor(THREADS/k) whole pixels of one problem instance, one
+// thread per (pixel, interval) record.  Shared by the single-instance kernels
+// and the batched kernels of lift_batch.cu.
+template <int KIND, int THREADS>
+__device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__restrict__ xbar,
+                                          float4 *__restrict__ y, float *__restrict__ q,
+                                          int tile, float *s_in, float *s_last)
 {
-    __shared__ float s_in[kStepThreads];
-    __shared__ float s_last[kStepThreads / 32];
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
-    const int pix = blockIdx.x * P.ppb + lp;
+    const int pix = tile * P.ppb + lp;
     const bool active = lp < P.ppb && pix < P.N;
     const size_t o = static_cast<size_t>(pix) * P.k + i;
 
@@ -133,16 +135,17 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     y[o] = make_float4(v, z, px, py);
 }
 
-__global__ void __launch_bounds__(kStepThreads)
-primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
-                   const float4 *__restrict__ y, const float *__restrict__ q)
+template <int THREADS>
+__device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restrict__ x,
+                                            float2 *__restrict__ xbar,
+                                            const float4 *__restrict__ y,
+                                            const float *__restrict__ q, int tile, float *s_in,
+                                            float *s_last)
 {
-    __shared__ float s_in[kStepThreads];
-    __shared__ float s_last[kStepThreads / 32];
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
-    const int pix = blockIdx.x * P.ppb + lp;
+    const int pix = tile * P.ppb + lp;
     const bool active = lp < P.ppb && pix < P.N;
     const size_t o = static_cast<size_t>(pix) * P.k + i;
 
@@ -172,6 +175,97 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     const float sn = xo.y - ic.y * (d.y - P.delta * qq + P.delta * head - ic.x * d.x);
     x[o] = make_float2(un, sn);
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kStepThreads)
+dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
+                 float *__restrict__ q)
+{
+    __shared__ float s_in[kStepThreads];
+    __shared__ float s_last[kStepThreads / 32];
+    dual_tile<KIND, kStepThreads>(P, xbar, y, q, blockIdx.x, s_in, s_last);
+}
+
+__global__ void __launch_bounds__(kStepThreads)
+primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
+                   const float4 *__restrict__ y, const float *__restrict__ q)
+{
+    __shared__ float s_in[kStepThreads];
+    __shared__ float s_last[kStepThreads / 32];
+    primal_tile<kStepThreads>(P, x, xbar, y, q, blockIdx.x, s_in, s_last);
+}
+
+// ---------------------------------------------------------------------------
+// Batched half-steps: many instances (each its own size, k and data) in one
+// launch.  Block b processes tile b - tile0 of instance tile_inst[b]; blocks
+// of instances whose flag in `live` is 0 (converged) return at once.
+// ---------------------------------------------------------------------------
+// The block's instance descriptor is staged once in shared memory, so the
+// tile body reads its parameters as broadcast shared loads.
+__device__ __forceinline__ void stage_desc(const InstDesc *__restrict__ D, int inst, InstDesc *sd)
+{
+    constexpr int words = static_cast<int>(sizeof(InstDesc) / sizeof(int));
+    static_assert(sizeof(InstDesc) % sizeof(int) == 0, "descriptor size");
+    const int *src = reinterpret_cast<const int *>(D + inst);
+    int *dst = reinterpret_cast<int *>(sd);
+    for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = __ldg(src + j);
+    __syncthreads();
+}
+
+template <int KIND, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
+batch_dual_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile_inst,
+                  const int *__restrict__ live)
+{
+    __shared__ float s_in[THREADS];
+    __shared__ float s_last[THREADS / 32];
+    __shared__ InstDesc sd;
+    const int inst = tile_inst[blockIdx.x];
+    if (!live[inst]) return;
+    stage_desc(D, inst, &sd);
+    dual_tile<KIND, THREADS>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, blockIdx.x - sd.tile0, s_in, s_last);
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
+batch_primal_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile_inst,
+                    const int *__restrict__ live)
+{
+    __shared__ float s_in[THREADS];
+    __shared__ float s_last[THREADS / 32];
+    __shared__ InstDesc sd;
+    const int inst = tile_inst[blockIdx.x];
+    if (!live[inst]) return;
+    stage_desc(D, inst, &sd);
+    primal_tile<THREADS>(sd.P, sd.S.x, sd.S.xbar, sd.S.y, sd.S.q, blockIdx.x - sd.tile0, s_in,
+                         s_last);
+}
+
+template <int THREADS>
+static cudaError_t launch_batch_t(int kind, const InstDesc *D, const int *tile_inst,
+                                  const int *live, int ntiles, cudaStream_t st)
+{
+    if (kind == 2)
+        batch_dual_kernel<2, THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
+    else
+        batch_dual_kernel<0, THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_primal_kernel<THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iteration(int kind, int threads, const InstDesc *D, const int *tile_inst,
+                                   const int *live, int ntiles, cudaStream_t st)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    switch (threads) {
+    case 128: return launch_batch_t<128>(kind, D, tile_inst, live, ntiles, st);
+    case 256: return launch_batch_t<256>(kind, D, tile_inst, live, ntiles, st);
+    case 512: return launch_batch_t<512>(kind, D, tile_inst, live, ntiles, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 static inline int step_blocks(const LiftParams &P)

@@ -26,6 +26,9 @@ EXPORTED = (
     "lift_energy", "lift_gap", "lift_unlift", "lift_state_bytes", "lift_get_state",
     "lift_set_state", "lift_proj_epi", "lift_envelope", "lift_strerror",
     "lift_energy_noalloc",
+    "lift_create_batch", "lift_batch_destroy", "lift_batch_size", "lift_batch_reset",
+    "lift_batch_iterate", "lift_batch_solve", "lift_batch_energy", "lift_batch_unlift",
+    "lift_batch_get_state", "lift_batch_autotune",
 )
 
 
@@ -77,6 +80,16 @@ def load(path: str = LIB_PATH):
         "lift_envelope": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "lift_strerror": (C.c_char_p, [C.c_int]),
         "lift_energy_noalloc": (C.c_int, [C.POINTER(lift_spec), vp, vp, vp]),
+        "lift_create_batch": (C.c_int, [C.POINTER(lift_spec), C.c_int, vp, C.POINTER(vp)]),
+        "lift_batch_destroy": (None, [vp]),
+        "lift_batch_size": (C.c_int, [vp]),
+        "lift_batch_reset": (C.c_int, [vp]),
+        "lift_batch_iterate": (C.c_int, [vp, C.c_int]),
+        "lift_batch_solve": (C.c_int, [vp, C.c_int, C.c_double, ip, ip]),
+        "lift_batch_energy": (C.c_int, [vp, dp]),
+        "lift_batch_unlift": (C.c_int, [vp, C.c_int, vp, C.c_int]),
+        "lift_batch_get_state": (C.c_int, [vp, C.c_int, vp, C.c_size_t, C.c_int]),
+        "lift_batch_autotune": (C.c_int, [vp, C.c_int, ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,3 +326,68 @@ class Solver:
         buf = np.ascontiguousarray(np.concatenate([x, xb, y, q]))
         assert buf.size * 4 == lift_state_bytes(self.h) and N * k > 0
         lift_set_state(self.h, buf)
+
+
+# ---------------------------------------------------------------------------
+# Batches
+# ---------------------------------------------------------------------------
+def lift_create_batch(specs: list, stream: int | None = None) -> int:
+    arr = (lift_spec * len(specs))(*specs)
+    h = C.c_void_p()
+    s = current_stream() if stream is None else stream
+    _check(load().lift_create_batch(arr, len(specs), C.c_void_p(s), C.byref(h)),
+           "lift_create_batch")
+    return h.value
+
+
+def lift_batch_destroy(b: int) -> None:
+    load().lift_batch_destroy(C.c_void_p(b))
+
+
+def lift_batch_size(b: int) -> int:
+    return load().lift_batch_size(C.c_void_p(b))
+
+
+def lift_batch_reset(b: int) -> None:
+    _check(load().lift_batch_reset(C.c_void_p(b)), "lift_batch_reset")
+
+
+def lift_batch_iterate(b: int, iters: int) -> None:
+    _check(load().lift_batch_iterate(C.c_void_p(b), iters), "lift_batch_iterate")
+
+
+def lift_batch_solve(b: int, max_iters: int, rel_gap_tol: float):
+    """(status, per-instance iterations, number converged)."""
+    n = lift_batch_size(b)
+    it = (C.c_int * n)()
+    nc = C.c_int()
+    rc = load().lift_batch_solve(C.c_void_p(b), max_iters, rel_gap_tol, it, C.byref(nc))
+    if rc not in (LIFT_OK, LIFT_ERR_NOT_CONVERGED):
+        raise LiftError(rc, "lift_batch_solve")
+    return rc, list(it), nc.value
+
+
+def lift_batch_energy(b: int) -> np.ndarray:
+    n = lift_batch_size(b)
+    out = np.empty(3 * n, dtype=np.float64)
+    _check(load().lift_batch_energy(C.c_void_p(b), out.ctypes.data_as(C.POINTER(C.c_double))),
+           "lift_batch_energy")
+    return out.reshape(n, 3)
+
+
+def lift_batch_unlift(b: int, i: int, out) -> None:
+    p, on_host = _ptr(out)
+    _check(load().lift_batch_unlift(C.c_void_p(b), i, C.c_void_p(p), on_host), "lift_batch_unlift")
+
+
+def lift_batch_get_state(b: int, i: int, dst) -> None:
+    p, on_host = _ptr(dst)
+    nbytes = dst.nbytes if isinstance(dst, np.ndarray) else dst.numel() * dst.element_size()
+    _check(load().lift_batch_get_state(C.c_void_p(b), i, C.c_void_p(p), nbytes, on_host),
+           "lift_batch_get_state")
+
+
+def lift_batch_autotune(b: int, iters: int) -> int:
+    t = C.c_int()
+    _check(load().lift_batch_autotune(C.c_void_p(b), iters, C.byref(t)), "lift_batch_autotune")
+    return t.value
