@@ -180,6 +180,34 @@ int lift_proj_epi(lift_handle h, const int *pix, const int *interval,
 int lift_envelope(lift_handle h, const int *pix, const int *interval,
                   const float *t, float *out, int n);
 
+/* ------------------------------------------------------- differentiation */
+/* The unrolled solve as a differentiable map (the paper has none): from the
+ * zero state, `iters` iterations map (f, lambda, alpha, nu) to the unlifted
+ * image u~.  The reverse pass is hand-written (adjoint.cu): it pulls the
+ * adjoint back through each half-step, including the clamp, the l2-ball
+ * projection and the epigraph projections (derivatives taken on the branch
+ * that the forward pass took; the map is piecewise smooth).  Quadratic and
+ * truncated-quadratic data terms only. */
+
+/* lift_set_params: change lambda, alpha and nu of an existing handle (the
+ * step sizes do not depend on them).  LIFT_ERR_SPEC for invalid values. */
+int lift_set_params(lift_handle h, double lambda, double alpha, double nu);
+
+/* lift_unrolled_forward: reset, then run `iters` iterations, storing the
+ * state every `checkpoint_every` iterations (ceil(iters/checkpoint_every)
+ * state copies of lift_state_bytes each, kept by the handle).  The final
+ * state is the handle's state (lift_unlift reads it).  Asynchronous. */
+int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every);
+
+/* lift_unrolled_backward: given grad_u = dL/du~ (device, H*W) for the image
+ * of the last lift_unrolled_forward, write dL/df to grad_f (device, H*W; may
+ * be NULL) and {dL/dlambda, dL/dalpha, dL/dnu} to grad_scalars (host, 3
+ * doubles; may be NULL).  Each segment between checkpoints is recomputed
+ * forward into a buffer of checkpoint_every + 1 states, then pulled back.
+ * Synchronises when grad_scalars is requested. */
+int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f,
+                           double *grad_scalars);
+
 /* --------------------------------------------------------------- batches */
 /* A batch solves many independent problems (each its own size, label count
  * and data; one data-term kind, LIFT_QUAD or LIFT_TRUNC_QUAD) together: each

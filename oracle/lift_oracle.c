@@ -39,6 +39,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#define LIFT_ORACLE_MAXK 256
+
 /* ------------------------------------------------------------------------ */
 /* Problem description (owned by the caller, read-only here).               */
 /* ------------------------------------------------------------------------ */
@@ -611,4 +613,188 @@ double orc_rof_energy(int H, int W, const double *u, const double *f,
                       double alpha, double lam)
 {
     return rof_primal(H, W, u, f, alpha, lam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode through `iters` unrolled PDHG iterations from the zero       */
+/* state (the differentiable solve; not part of the paper).  Given           */
+/* g_u = dL/du~ of the final unlifted image u~ = gamma_1 + sum_i Delta u_i,   */
+/* returns dL/df (per pixel) and dL/d{lambda, alpha, nu}.                     */
+/* All states are stored; each step is pulled back in reverse order.  The    */
+/* local Jacobians of the epigraph projections (w.r.t. the projected point   */
+/* and f, alpha, nu) are taken by central differences of orc_proj_epi in     */
+/* FP64; the clamp and the l2-ball projection are differentiated by hand.   */
+/* Kinks of the unrolled map (clamp bounds, ball boundary, projection-region */
+/* boundaries) are taken as not hit.                                          */
+/* ------------------------------------------------------------------------ */
+static void proj_jacobian(const orc_problem *P, int pix, int i, double y0, double h0,
+                          double J[2][5])
+{
+    /* columns: y0, h0, f(pix), alpha, nu */
+    orc_problem Q = *P;
+    double fv = P->f ? P->f[pix] : 0.0;
+    double base[5] = {y0, h0, fv, P->alpha, P->nu};
+    for (int c = 0; c < 5; ++c) {
+        if (c >= 2 && P->kind == ORC_PL) { J[0][c] = J[1][c] = 0.0; continue; }
+        if (c == 4 && P->kind != ORC_TRUNC) { J[0][c] = J[1][c] = 0.0; continue; }
+        double hstep = 1e-8 * (1.0 + fabs(base[c]));
+        double out[2][2];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            double a[5] = {base[0], base[1], base[2], base[3], base[4]};
+            a[c] += sgn ? hstep : -hstep;
+            double fl = a[2];
+            Q.f = &fl;
+            Q.alpha = a[3];
+            Q.nu = a[4];
+            double yo, ho;
+            orc_proj_epi(&Q, 0, i, a[0], a[1], &yo, &ho);
+            out[sgn][0] = yo;
+            out[sgn][1] = ho;
+        }
+        J[0][c] = (out[1][0] - out[0][0]) / (2.0 * hstep);
+        J[1][c] = (out[1][1] - out[0][1]) / (2.0 * hstep);
+    }
+}
+
+int orc_unrolled_grad(const orc_problem *P, int iters, const double *g_u, double *grad_f,
+                      double *grad_scal)
+{
+    int H = P->H, W = P->W, k = P->L - 1;
+    size_t N = (size_t)H * W, Nk = N * k;
+    if (P->kind == ORC_PL) return -2;
+    orc_steps S;
+    make_steps(P, &S);
+    /* stored states: per state u,s,ubar,sbar,v,z,px,py (Nk each) + q (N) */
+    size_t per = 8 * Nk + N;
+    double *st = (double *)calloc(per * (size_t)(iters + 1), sizeof(double));
+    double *ax = (double *)calloc(2 * Nk, sizeof(double));   /* u, s */
+    double *axb = (double *)calloc(2 * Nk, sizeof(double));  /* ubar, sbar */
+    double *ay = (double *)calloc(4 * Nk, sizeof(double));   /* v, z, px, py */
+    double *aq = (double *)calloc(N, sizeof(double));
+    double *gu = (double *)calloc(Nk, sizeof(double));
+    double *gs = (double *)calloc(Nk, sizeof(double));
+    double *Aa = (double *)calloc(2 * Nk, sizeof(double));
+    double *dv = (double *)malloc(sizeof(double) * Nk);
+    if (!st || !ax || !axb || !ay || !aq || !gu || !gs || !Aa || !dv) {
+        free(st); free(ax); free(axb); free(ay); free(aq); free(gu); free(gs); free(Aa); free(dv);
+        free_steps(&S);
+        return -1;
+    }
+#define ST(n, f) (st + (size_t)(n) * per + (size_t)(f) * Nk)
+    /* forward, keeping every state (state 0 = all zeros) */
+    for (int n = 0; n < iters; ++n) {
+        memcpy(ST(n + 1, 0), ST(n, 0), sizeof(double) * per);
+        orc_state X = {ST(n + 1, 0), ST(n + 1, 1), ST(n + 1, 2), ST(n + 1, 3), ST(n + 1, 4),
+                       ST(n + 1, 5), ST(n + 1, 6), ST(n + 1, 7), ST(n + 1, 8)};
+        orc_pdhg(P, &X, 1);
+    }
+    /* seed: dL/du_i = Delta_i dL/du~ */
+    for (size_t pix = 0; pix < N; ++pix)
+        for (int i = 0; i < k; ++i)
+            ax[2 * (pix * k + i)] = (gam(P, i + 1) - gam(P, i)) * g_u[pix];
+    for (size_t pix = 0; pix < N; ++pix) grad_f[pix] = 0.0;
+    grad_scal[0] = grad_scal[1] = grad_scal[2] = 0.0;
+
+    for (int n = iters - 1; n >= 0; --n) {
+        const double *u0 = ST(n, 0), *ub0 = ST(n, 2), *sb0 = ST(n, 3);
+        const double *v0 = ST(n, 4), *z0 = ST(n, 5), *px0 = ST(n, 6), *py0 = ST(n, 7);
+        const double *v1 = ST(n + 1, 4), *px1 = ST(n + 1, 6), *py1 = ST(n + 1, 7);
+        /* ---- primal step: u' = clamp(u - tau_u (v - div p)), s' = ..., xbar' = 2x' - x */
+        orc_div(H, W, k, px1, py1, dv);
+        for (size_t o = 0; o < Nk; ++o) {
+            double w = u0[o] - S.tau_u * (v1[o] - dv[o]);
+            double m = (w > 0.0 && w < 1.0) ? 1.0 : 0.0;
+            gu[o] = m * (ax[2 * o] + 2.0 * axb[2 * o]);
+            gs[o] = ax[2 * o + 1] + 2.0 * axb[2 * o + 1];
+            ax[2 * o] = gu[o] - axb[2 * o];
+            ax[2 * o + 1] = gs[o] - axb[2 * o + 1];
+        }
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t pix = (size_t)y * W + x;
+                for (int l = 0; l < k; ++l) {
+                    size_t o = pix * k + l;
+                    double d = gam(P, l + 1) - gam(P, l);
+                    /* s_i uses v_l (l < i) through Delta * sum_{l<i} v_l and v_i through -gamma_i v_i */
+                    double acc = -S.tau_u * gu[o] + S.tau_s[l] * gam(P, l) * gs[o];
+                    for (int i = l + 1; i < k; ++i)
+                        acc -= S.tau_s[i] * (gam(P, i + 1) - gam(P, i)) * gs[pix * k + i];
+                    ay[4 * o + 0] += acc;
+                    ay[4 * o + 1] += -S.tau_s[l] * gs[o];
+                    aq[pix] += S.tau_s[l] * d * gs[o];
+                    /* div p = -grad^T p: d u'/d px(x) = tau_u ([x<W-1] g(x) - g(x+1)) */
+                    if (x + 1 < W) ay[4 * o + 2] += S.tau_u * (gu[o] - gu[o + k]);
+                    if (y + 1 < H) ay[4 * o + 3] += S.tau_u * (gu[o] - gu[o + (size_t)W * k]);
+                }
+            }
+        /* ---- dual step from (xbar_n, y_n, q_n) */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                size_t pix = (size_t)y * W + x;
+                double adjv[LIFT_ORACLE_MAXK];
+                for (int i = 0; i < k; ++i) {
+                    size_t o = pix * k + i;
+                    double d = gam(P, i + 1) - gam(P, i);
+                    /* TV part */
+                    double gx = x + 1 < W ? ub0[o + k] - ub0[o] : 0.0;
+                    double gy = y + 1 < H ? ub0[o + (size_t)W * k] - ub0[o] : 0.0;
+                    double a0 = px0[o] + S.sigma_p * gx, a1 = py0[o] + S.sigma_p * gy;
+                    double nrm = sqrt(a0 * a0 + a1 * a1), R = P->lam * d;
+                    double ap0 = ay[4 * o + 2], ap1 = ay[4 * o + 3];
+                    double aa0 = ap0, aa1 = ap1;
+                    if (nrm > R) {
+                        double h0 = a0 / nrm, h1 = a1 / nrm, dot = h0 * ap0 + h1 * ap1;
+                        aa0 = (R / nrm) * (ap0 - h0 * dot);
+                        aa1 = (R / nrm) * (ap1 - h1 * dot);
+                        grad_scal[0] += d * dot;
+                    }
+                    Aa[2 * o] = aa0;
+                    Aa[2 * o + 1] = aa1;
+                    /* data part: v^ = v + sigma (ubar + Delta sum_{j>i} sbar_j - gamma_i sbar_i),
+                       z^ = z + sigma sbar, (v', z') = Delta Proj((v^, z^)/Delta) */
+                    double tail = 0.0;
+                    for (int j = i + 1; j < k; ++j) tail += (gam(P, j + 1) - gam(P, j)) * sb0[pix * k + j];
+                    double vh = v0[o] + S.sigma_vz[i] * (ub0[o] + tail - gam(P, i) * sb0[o]);
+                    double zh = z0[o] + S.sigma_vz[i] * sb0[o];
+                    double J[2][5];
+                    proj_jacobian(P, (int)pix, i, vh / d, zh / d, J);
+                    double avv = ay[4 * o], avz = ay[4 * o + 1];
+                    double adv = avv * J[0][0] + avz * J[1][0];
+                    double adz = avv * J[0][1] + avz * J[1][1];
+                    grad_f[pix] += d * (avv * J[0][2] + avz * J[1][2]);
+                    grad_scal[1] += d * (avv * J[0][3] + avz * J[1][3]);
+                    grad_scal[2] += d * (avv * J[0][4] + avz * J[1][4]);
+                    adjv[i] = adv;
+                    ay[4 * o + 0] = adv;
+                    ay[4 * o + 1] = adz;
+                    ay[4 * o + 2] = aa0;
+                    ay[4 * o + 3] = aa1;
+                    /* adjoint of xbar_n: own terms */
+                    double au = S.sigma_vz[i] * adv;
+                    if (x + 1 < W) au -= S.sigma_p * aa0;
+                    if (y + 1 < H) au -= S.sigma_p * aa1;
+                    axb[2 * o] = au;
+                    axb[2 * o + 1] = -S.sigma_vz[i] * gam(P, i) * adv + S.sigma_vz[i] * adz
+                                     - S.sigma_q * d * aq[pix];
+                }
+                /* sbar_j enters v^_l (l < j) through the tail sums */
+                for (int j = 0; j < k; ++j) {
+                    double dj = gam(P, j + 1) - gam(P, j), acc = 0.0;
+                    for (int l = 0; l < j; ++l) acc += S.sigma_vz[l] * adjv[l];
+                    axb[2 * (pix * k + j) + 1] += dj * acc;
+                }
+            }
+        /* neighbours' part of grad^T: a(x-1) and a(x-W) used ubar(x) */
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int i = 0; i < k; ++i) {
+                    size_t o = ((size_t)y * W + x) * k + i;
+                    if (x > 0) axb[2 * o] += S.sigma_p * Aa[2 * (o - k)];
+                    if (y > 0) axb[2 * o] += S.sigma_p * Aa[2 * (o - (size_t)W * k) + 1];
+                }
+    }
+#undef ST
+    free(st); free(ax); free(axb); free(ay); free(aq); free(gu); free(gs); free(Aa); free(dv);
+    free_steps(&S);
+    return 0;
 }

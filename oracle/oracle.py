@@ -82,6 +82,8 @@ def _load():
         lib.orc_rof_direct.restype = C.c_double
         lib.orc_rof_direct.argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_int, _dp]
+        lib.orc_unrolled_grad.restype = C.c_int
+        lib.orc_unrolled_grad.argtypes = [P, C.c_int, _dp, _dp, _dp]
         lib.orc_rof_energy.restype = C.c_double
         lib.orc_rof_energy.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double]
         _lib = lib
@@ -256,3 +258,14 @@ def rof_energy(u: np.ndarray, f: np.ndarray, alpha: float, lam: float) -> float:
     u = np.ascontiguousarray(u, dtype=np.float64)
     fd = np.ascontiguousarray(f, dtype=np.float64)
     return _load().orc_rof_energy(H, W, _ptr(u), _ptr(fd), alpha, lam)
+
+
+def unrolled_grad(P: Problem, iters: int, g_u: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Reverse pass through `iters` iterations from zero: given dL/du~ of the
+    final unlifted image, (dL/df [N], dL/d(lambda, alpha, nu) [3])."""
+    g = np.ascontiguousarray(g_u, dtype=np.float64).reshape(P.N)
+    gf, gs = np.zeros(P.N), np.zeros(3)
+    rc = _load().orc_unrolled_grad(P.ref(), iters, _ptr(g), _ptr(gf), _ptr(gs))
+    if rc != 0:
+        raise RuntimeError(f"oracle unrolled_grad failed ({rc})")
+    return gf, gs

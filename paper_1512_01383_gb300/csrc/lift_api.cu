@@ -32,6 +32,12 @@ struct lift_ctx {
     double *dout = nullptr;    // energy sums (device)
     double *hout = nullptr;    // energy sums (pinned host)
     size_t data_elems = 0;     // N (quadratic) or N*ns (PL)
+    // differentiable solve
+    char *ckpt = nullptr;      // checkpoints: states at iterations 0, C, 2C, ...
+    char *seg = nullptr;       // one segment's states, recomputed in the backward pass
+    int unrolled_iters = 0, ckpt_every = 0, ckpt_count = 0, seg_cap = 0;
+    lift::AdjState adj{};
+    void *adj_arena = nullptr;
 };
 
 namespace {
@@ -60,6 +66,9 @@ void free_ctx(lift_ctx *h)
                     h->bpos, h->bstart, h->ubuf, h->partial, h->dout};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->ckpt) cudaFree(h->ckpt);
+    if (h->seg) cudaFree(h->seg);
+    if (h->adj_arena) cudaFree(h->adj_arena);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
 }
@@ -819,6 +828,175 @@ int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen)
     if (rc == LIFT_OK) rc = lift_batch_reset(b);
     if (rc == LIFT_OK && threads_chosen) *threads_chosen = best;
     return rc;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Differentiable unrolled solve (adjoint.cu): checkpointed forward, reverse
+// sweep with per-segment recomputation.
+// ===========================================================================
+namespace {
+
+// Distance between consecutive stored states: the state image rounded up to
+// 256 bytes, so that every stored state starts aligned for the float2 /
+// float4 records (the image itself ends with N floats).
+size_t state_stride(lift_handle h)
+{
+    return (lift_state_bytes(h) + 255) & ~static_cast<size_t>(255);
+}
+
+LiftState state_at(const lift_ctx *h, char *base)
+{
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    LiftState S;
+    S.x = reinterpret_cast<float2 *>(base);
+    S.xbar = reinterpret_cast<float2 *>(base + Nk * sizeof(float2));
+    S.y = reinterpret_cast<float4 *>(base + 2 * Nk * sizeof(float2));
+    S.q = reinterpret_cast<float *>(base + 2 * Nk * sizeof(float2) + Nk * sizeof(float4));
+    return S;
+}
+
+int copy_state_dev(lift_handle h, const LiftState &dst, const LiftState &src)
+{
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    LIFT_CK(cudaMemcpyAsync(dst.x, src.x, Nk * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    LIFT_CK(cudaMemcpyAsync(dst.xbar, src.xbar, Nk * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    LIFT_CK(cudaMemcpyAsync(dst.y, src.y, Nk * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+    LIFT_CK(cudaMemcpyAsync(dst.q, src.q, h->N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return LIFT_OK;
+}
+
+int iterate_state(lift_handle h, const LiftState &S, int iters)
+{
+    for (int n = 0; n < iters; ++n) {
+        LIFT_CK(lift::launch_dual_step(h->P, S, h->stream));
+        LIFT_CK(lift::launch_primal_step(h->P, S, h->stream));
+    }
+    return LIFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
+{
+    if (!h) return LIFT_ERR_ARG;
+    if (!is_finite(lambda) || lambda < 0.0) return LIFT_ERR_SPEC;
+    if (h->kind != LIFT_PL_SAMPLED) {
+        if (!is_finite(alpha) || !(alpha > 0.0)) return LIFT_ERR_SPEC;
+        if (h->kind == LIFT_TRUNC_QUAD && (!is_finite(nu) || !(nu > 0.0))) return LIFT_ERR_SPEC;
+    }
+    std::vector<float4> ic(h->k);
+    LIFT_CK(cudaMemcpyAsync(ic.data(), h->icst, h->k * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < h->k; ++i) ic[i].w = static_cast<float>(lambda * h->P.delta);
+    LIFT_CK(cudaMemcpyAsync(h->icst, ic.data(), h->k * sizeof(float4), cudaMemcpyHostToDevice, h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));
+    h->P.lam = static_cast<float>(lambda);
+    if (h->kind != LIFT_PL_SAMPLED) {
+        h->P.alpha = static_cast<float>(alpha);
+        h->P.nu = static_cast<float>(nu);
+        h->P.wtrunc = h->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(nu / alpha)) : 0.0f;
+    }
+    return LIFT_OK;
+}
+
+int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every)
+{
+    if (!h || iters < 1 || checkpoint_every < 1) return LIFT_ERR_ARG;
+    if (h->kind == LIFT_PL_SAMPLED) return LIFT_ERR_SPEC;
+    const size_t sb = state_stride(h);
+    const int nck = (iters + checkpoint_every - 1) / checkpoint_every;
+    if (nck > h->ckpt_count) {
+        if (h->ckpt) cudaFree(h->ckpt);
+        h->ckpt = nullptr;
+        h->ckpt_count = 0;
+        const int rc = dev_alloc(reinterpret_cast<void **>(&h->ckpt), sb * nck);
+        if (rc != LIFT_OK) return rc;
+        h->ckpt_count = nck;
+    }
+    int rc = lift_reset(h);
+    if (rc != LIFT_OK) return rc;
+    for (int c = 0; c < nck; ++c) {
+        rc = copy_state_dev(h, state_at(h, h->ckpt + sb * c), h->S);
+        if (rc != LIFT_OK) return rc;
+        const int len = std::min(checkpoint_every, iters - c * checkpoint_every);
+        rc = iterate_state(h, h->S, len);
+        if (rc != LIFT_OK) return rc;
+    }
+    h->unrolled_iters = iters;
+    h->ckpt_every = checkpoint_every;
+    return LIFT_OK;
+}
+
+int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f, double *grad_scalars)
+{
+    if (!h || !grad_u) return LIFT_ERR_ARG;
+    if (h->unrolled_iters < 1) return LIFT_ERR_ARG;
+    const size_t sb = state_stride(h);
+    const size_t N = static_cast<size_t>(h->N), Nk = N * h->k;
+    const int C = h->ckpt_every;
+    if (C + 1 > h->seg_cap) {
+        if (h->seg) cudaFree(h->seg);
+        h->seg = nullptr;
+        h->seg_cap = 0;
+        const int rc = dev_alloc(reinterpret_cast<void **>(&h->seg), sb * (C + 1));
+        if (rc != LIFT_OK) return rc;
+        h->seg_cap = C + 1;
+    }
+    if (!h->adj_arena) {
+        const int nb = lift::adjoint_blocks(h->P);
+        size_t total = 0;
+        auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
+        const size_t o_ax = take(Nk * sizeof(float2)), o_axb = take(Nk * sizeof(float2));
+        const size_t o_ay = take(Nk * sizeof(float4)), o_aq = take(N * sizeof(float));
+        const size_t o_G = take(Nk * sizeof(float2)), o_A = take(Nk * sizeof(float2));
+        const size_t o_gf = take(N * sizeof(float)), o_p = take(3 * sizeof(double) * nb);
+        const size_t o_acc = take(3 * sizeof(double));
+        const int rc = dev_alloc(&h->adj_arena, total);
+        if (rc != LIFT_OK) return rc;
+        char *b = static_cast<char *>(h->adj_arena);
+        h->adj.ax = reinterpret_cast<float2 *>(b + o_ax);
+        h->adj.axb = reinterpret_cast<float2 *>(b + o_axb);
+        h->adj.ay = reinterpret_cast<float4 *>(b + o_ay);
+        h->adj.aq = reinterpret_cast<float *>(b + o_aq);
+        h->adj.G = reinterpret_cast<float2 *>(b + o_G);
+        h->adj.A = reinterpret_cast<float2 *>(b + o_A);
+        h->adj.gf = reinterpret_cast<float *>(b + o_gf);
+        h->adj.partial = reinterpret_cast<double *>(b + o_p);
+        h->adj.acc = reinterpret_cast<double *>(b + o_acc);
+    }
+    const lift::AdjState &A = h->adj;
+    LIFT_CK(lift::launch_adj_seed(h->P, grad_u, A.ax, h->stream));
+    LIFT_CK(cudaMemsetAsync(A.axb, 0, Nk * sizeof(float2), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.ay, 0, Nk * sizeof(float4), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.aq, 0, N * sizeof(float), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.gf, 0, N * sizeof(float), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.acc, 0, 3 * sizeof(double), h->stream));
+    const int nck = (h->unrolled_iters + C - 1) / C;
+    for (int c = nck - 1; c >= 0; --c) {
+        const int len = std::min(C, h->unrolled_iters - c * C);
+        // recompute the segment's states from its checkpoint
+        int rc = copy_state_dev(h, state_at(h, h->seg), state_at(h, h->ckpt + sb * c));
+        for (int j = 0; j < len && rc == LIFT_OK; ++j) {
+            rc = copy_state_dev(h, state_at(h, h->seg + sb * (j + 1)), state_at(h, h->seg + sb * j));
+            if (rc == LIFT_OK) rc = iterate_state(h, state_at(h, h->seg + sb * (j + 1)), 1);
+        }
+        if (rc != LIFT_OK) return rc;
+        for (int j = len - 1; j >= 0; --j)
+            LIFT_CK(lift::launch_adj_iteration(h->P, state_at(h, h->seg + sb * j),
+                                               state_at(h, h->seg + sb * (j + 1)), A, h->stream));
+    }
+    if (grad_f)
+        LIFT_CK(cudaMemcpyAsync(grad_f, A.gf, N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    if (grad_scalars) {
+        LIFT_CK(cudaMemcpyAsync(h->hout, A.acc, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        LIFT_CK(cudaStreamSynchronize(h->stream));
+        memcpy(grad_scalars, h->hout, 3 * sizeof(double));
+    }
+    return LIFT_OK;
 }
 
 }  // extern "C"

@@ -26,16 +26,26 @@ namespace lift {
 //   between :  c y + y^2 / (2a)              (parabola, slope t = c + y/a)
 // with kinks at m1 (slopes l -> t1) and m2 (t2 -> r) when t1 > l, t2 < r.
 // ---------------------------------------------------------------------------
-struct QPiece {
-    float l, r, A, B, m1, m2, t1, t2, a, c;
+// Scalar helpers: T is float on the solver path, or a forward-mode dual
+// number (lift_ad.cuh) when the adjoint needs the Jacobian of a projection.
+__device__ __forceinline__ float val(float x) { return x; }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float tsqrt(float a) { return sqrtf(a); }
+
+template <class T>
+struct QPieceT {
+    T l, r, A, B, m1, m2, t1, t2, a, c;
     bool arc;
 };
+using QPiece = QPieceT<float>;
 
 // rho = alpha/2 (t - f)^2: the piece is the parabola itself.
-__device__ __forceinline__ QPiece make_quad_piece(float alpha, float f, float l, float r)
+template <class T>
+__device__ __forceinline__ QPieceT<T> make_quad_piece(T alpha, T f, float l, float r)
 {
-    QPiece q;
-    q.l = l; q.r = r; q.a = alpha; q.c = f; q.t1 = l; q.t2 = r; q.arc = true;
+    QPieceT<T> q;
+    q.l = T(l); q.r = T(r); q.a = alpha; q.c = f; q.t1 = T(l); q.t2 = T(r); q.arc = true;
     q.m1 = alpha * (l - f);
     q.m2 = alpha * (r - f);
     q.A = 0.5f * alpha * (l - f) * (l - f);
@@ -51,56 +61,58 @@ __device__ __forceinline__ QPiece make_quad_piece(float alpha, float f, float l,
 // end points, and an interval entirely in a constant part is constant.
 // Tangent from (l, nu): with e = f - l > w, the touching point f + d solves
 // alpha d^2 + 2 alpha d e + nu = 0, d = -e + sqrt(e^2 - w^2) = -w^2/(e + sqrt(e^2 - w^2)).
-__device__ __forceinline__ QPiece make_trunc_piece(float alpha, float nu, float w, float f,
-                                                   float l, float r)
+template <class T>
+__device__ __forceinline__ QPieceT<T> make_trunc_piece(T alpha, T nu, T w, T f, float l, float r)
 {
-    QPiece q;
-    q.l = l; q.r = r; q.a = 2.0f * alpha; q.c = f;
-    const float kl = f - w, kr = f + w;
-    if (r <= kl || l >= kr) {
-        q.A = nu; q.B = nu; q.m1 = 0.0f; q.m2 = 0.0f; q.t1 = l; q.t2 = r; q.arc = false;
+    QPieceT<T> q;
+    q.l = T(l); q.r = T(r); q.a = 2.0f * alpha; q.c = f;
+    const T kl = f - w, kr = f + w;
+    if (r <= val(kl) || l >= val(kr)) {
+        q.A = nu; q.B = nu; q.m1 = T(0.0f); q.m2 = T(0.0f); q.t1 = T(l); q.t2 = T(r); q.arc = false;
         return q;
     }
-    const float w2 = w * w;
-    if (l >= kl) {
-        q.t1 = l; q.A = alpha * (l - f) * (l - f); q.m1 = 2.0f * alpha * (l - f);
+    const T w2 = w * w;
+    if (l >= val(kl)) {
+        q.t1 = T(l); q.A = alpha * (l - f) * (l - f); q.m1 = 2.0f * alpha * (l - f);
     } else {
-        const float e = f - l;
-        const float d = -w2 / (e + sqrtf(fmaxf(e * e - w2, 0.0f)));
+        const T e = f - l;
+        const T d = -w2 / (e + tsqrt(tmax(e * e - w2, T(0.0f))));
         q.t1 = f + d; q.A = nu; q.m1 = 2.0f * alpha * d;
     }
-    if (r <= kr) {
-        q.t2 = r; q.B = alpha * (r - f) * (r - f); q.m2 = 2.0f * alpha * (r - f);
+    if (r <= val(kr)) {
+        q.t2 = T(r); q.B = alpha * (r - f) * (r - f); q.m2 = 2.0f * alpha * (r - f);
     } else {
-        const float e = r - f;
-        const float d = w2 / (e + sqrtf(fmaxf(e * e - w2, 0.0f)));
+        const T e = r - f;
+        const T d = w2 / (e + tsqrt(tmax(e * e - w2, T(0.0f))));
         q.t2 = f + d; q.B = nu; q.m2 = 2.0f * alpha * d;
     }
     q.arc = true;
-    if (q.t1 > q.t2) {  // the tangent point lies beyond the far end: chord
-        const float rl = (l >= kl) ? alpha * (l - f) * (l - f) : nu;
-        const float rr = (r <= kr) ? alpha * (r - f) * (r - f) : nu;
+    if (val(q.t1) > val(q.t2)) {  // the tangent point lies beyond the far end: chord
+        const T rl = (l >= val(kl)) ? alpha * (l - f) * (l - f) : nu;
+        const T rr = (r <= val(kr)) ? alpha * (r - f) * (r - f) : nu;
         q.A = rl; q.B = rr;
         q.m1 = q.m2 = (rr - rl) / (r - l);
-        q.t1 = l; q.t2 = r;
+        q.t1 = T(l); q.t2 = T(r);
         q.arc = false;
     }
     return q;
 }
 
-__device__ __forceinline__ float qpiece_conj(const QPiece &q, float y)
+template <class T>
+__device__ __forceinline__ T qpiece_conj(const QPieceT<T> &q, T y)
 {
-    if (y <= q.m1) return q.l * y - q.A;
-    if (y >= q.m2) return q.r * y - q.B;
+    if (val(y) <= val(q.m1)) return q.l * y - q.A;
+    if (val(y) >= val(q.m2)) return q.r * y - q.B;
     return q.c * y + y * y / (2.0f * q.a);
 }
 
-__device__ __forceinline__ float qpiece_envelope(const QPiece &q, float t)
+template <class T>
+__device__ __forceinline__ T qpiece_envelope(const QPieceT<T> &q, T t)
 {
-    t = fminf(fmaxf(t, q.l), q.r);
-    if (!q.arc || t <= q.t1) return q.A + q.m1 * (t - q.l);
-    if (t >= q.t2) return q.B + q.m2 * (t - q.r);
-    const float d = t - q.c;
+    t = tmin(tmax(t, q.l), q.r);
+    if (!q.arc || val(t) <= val(q.t1)) return q.A + q.m1 * (t - q.l);
+    if (val(t) >= val(q.t2)) return q.B + q.m2 * (t - q.r);
+    const T d = t - q.c;
     return 0.5f * q.a * d * d;
 }
 
@@ -130,38 +142,40 @@ __device__ __forceinline__ float cubic_outer_root(float p, float Q)
 // left ray, the left kink, the parabola, the right kink or the right ray.
 // On a ray the projection is onto a line; on the parabola, with
 // w = c + y/a, G'(y) = (a/2)(w^3 + p w + q) with p = 2 - c^2 - 2 h0/a,
-// q = -2 (c + y0/a), and the projection is its outermost root (the one on
-// the side of -q), polished by one Newton step.
-__device__ __forceinline__ void qpiece_project(const QPiece &q, float y0, float h0,
-                                               float &yo, float &ho)
+// q = -2 (c + y0/a), and the projection is its outermost root (the side of
+// -q), polished by one Newton step.  (For a dual-number T the closed-form
+// root enters as a constant; the Newton step then carries the derivative of
+// the root by the implicit-function theorem.)
+template <class T>
+__device__ __forceinline__ void qpiece_project(const QPieceT<T> &q, T y0, T h0, T &yo, T &ho)
 {
-    const float phi0 = qpiece_conj(q, y0);
-    if (h0 >= phi0) { yo = y0; ho = h0; return; }
-    const float ph1 = q.l * q.m1 - q.A;             // rho_i^*(m1)
-    const float e1 = fmaxf(ph1 - h0, 0.0f);
-    if (q.m1 - y0 + e1 * q.l > 0.0f) {              // left ray
-        const float y = (y0 + q.l * (h0 + q.A)) / (1.0f + q.l * q.l);
+    const T phi0 = qpiece_conj(q, y0);
+    if (val(h0) >= val(phi0)) { yo = y0; ho = h0; return; }
+    const T ph1 = q.l * q.m1 - q.A;             // rho_i^*(m1)
+    const T e1 = tmax(ph1 - h0, T(0.0f));
+    if (val(q.m1 - y0 + e1 * q.l) > 0.0f) {     // left ray
+        const T y = (y0 + q.l * (h0 + q.A)) / (1.0f + q.l * q.l);
         yo = y; ho = q.l * y - q.A; return;
     }
-    const float ph2 = q.r * q.m2 - q.B;             // rho_i^*(m2)
-    const float e2 = fmaxf(ph2 - h0, 0.0f);
-    if (q.m2 - y0 + e2 * q.r < 0.0f) {              // right ray
-        const float y = (y0 + q.r * (h0 + q.B)) / (1.0f + q.r * q.r);
+    const T ph2 = q.r * q.m2 - q.B;             // rho_i^*(m2)
+    const T e2 = tmax(ph2 - h0, T(0.0f));
+    if (val(q.m2 - y0 + e2 * q.r) < 0.0f) {     // right ray
+        const T y = (y0 + q.r * (h0 + q.B)) / (1.0f + q.r * q.r);
         yo = y; ho = q.r * y - q.B; return;
     }
-    if (!q.arc || q.m1 - y0 + e1 * q.t1 >= 0.0f) { yo = q.m1; ho = ph1; return; }
-    if (q.m2 - y0 + e2 * q.t2 <= 0.0f) { yo = q.m2; ho = ph2; return; }
+    if (!q.arc || val(q.m1 - y0 + e1 * q.t1) >= 0.0f) { yo = q.m1; ho = ph1; return; }
+    if (val(q.m2 - y0 + e2 * q.t2) <= 0.0f) { yo = q.m2; ho = ph2; return; }
     // parabola arc
-    const float ia = 1.0f / q.a;
-    const float p = 2.0f - q.c * q.c - 2.0f * h0 * ia;
-    const float qq = -2.0f * (q.c + y0 * ia);
-    const float sg = qq <= 0.0f ? 1.0f : -1.0f;
-    float w = sg * cubic_outer_root(p, fabsf(qq));
-    w = fminf(fmaxf(w, q.t1), q.t2);
-    const float F = (w * w + p) * w + qq;
-    const float dF = 3.0f * w * w + p;
-    if (dF > 0.0f) w = fminf(fmaxf(w - F / dF, q.t1), q.t2);
-    const float y = q.a * (w - q.c);
+    const T ia = 1.0f / q.a;
+    const T p = 2.0f - q.c * q.c - 2.0f * h0 * ia;
+    const T qq = -2.0f * (q.c + y0 * ia);
+    const float sg = val(qq) <= 0.0f ? 1.0f : -1.0f;
+    T w = T(sg * cubic_outer_root(val(p), fabsf(val(qq))));
+    w = tmin(tmax(w, q.t1), q.t2);
+    const T F = (w * w + p) * w + qq;
+    const T dF = 3.0f * w * w + p;
+    if (val(dF) > 0.0f) w = tmin(tmax(w - F / dF, q.t1), q.t2);
+    const T y = q.a * (w - q.c);
     yo = y;
     ho = 0.5f * q.a * (w * w - q.c * q.c);
 }
@@ -224,8 +238,8 @@ __device__ __forceinline__ void pl_project(const float *__restrict__ t,
 __device__ __forceinline__ QPiece make_qpiece(const LiftParams &P, int pix, float l, float r)
 {
     const float f = __ldg(P.f + pix);
-    return P.kind == 0 ? make_quad_piece(P.alpha, f, l, r)
-                       : make_trunc_piece(P.alpha, P.nu, P.wtrunc, f, l, r);
+    return P.kind == 0 ? make_quad_piece<float>(P.alpha, f, l, r)
+                       : make_trunc_piece<float>(P.alpha, P.nu, P.wtrunc, f, l, r);
 }
 
 // rho_i^*(y) of pixel pix, interval i, for any kind.

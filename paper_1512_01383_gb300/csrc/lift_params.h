@@ -49,6 +49,17 @@ struct InstDesc {
     int tile0, ntiles;
 };
 
+// Adjoint buffers of the differentiable solve (adjoint.cu).
+struct AdjState {
+    float2 *ax, *axb;   // adjoints of x and xbar
+    float4 *ay;         // adjoint of y
+    float *aq;          // adjoint of q
+    float2 *G, *A;      // per-iteration temporaries for the neighbour gathers
+    float *gf;          // dL/df accumulated per pixel
+    double *partial;    // per-block scalar partials
+    double *acc;        // {dL/dlambda, dL/dalpha, dL/dnu}
+};
+
 constexpr int kStepThreads = 256;
 
 // pdhg_step.cu
@@ -57,6 +68,12 @@ cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStre
 
 cudaError_t launch_batch_iteration(int kind, int threads, const InstDesc *D, const int *tile_inst,
                                    const int *live, int ntiles, cudaStream_t st);
+
+// adjoint.cu
+int adjoint_blocks(const LiftParams &P);
+cudaError_t launch_adj_seed(const LiftParams &P, const float *grad_u, float2 *ax, cudaStream_t st);
+cudaError_t launch_adj_iteration(const LiftParams &P, const LiftState &Sn, const LiftState &Sn1,
+                                 const AdjState &A, cudaStream_t st);
 
 // setup_reduce.cu
 cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);

@@ -29,6 +29,7 @@ EXPORTED = (
     "lift_create_batch", "lift_batch_destroy", "lift_batch_size", "lift_batch_reset",
     "lift_batch_iterate", "lift_batch_solve", "lift_batch_energy", "lift_batch_unlift",
     "lift_batch_get_state", "lift_batch_autotune",
+    "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
 )
 
 
@@ -90,6 +91,9 @@ def load(path: str = LIB_PATH):
         "lift_batch_unlift": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "lift_batch_get_state": (C.c_int, [vp, C.c_int, vp, C.c_size_t, C.c_int]),
         "lift_batch_autotune": (C.c_int, [vp, C.c_int, ip]),
+        "lift_set_params": (C.c_int, [vp, C.c_double, C.c_double, C.c_double]),
+        "lift_unrolled_forward": (C.c_int, [vp, C.c_int, C.c_int]),
+        "lift_unrolled_backward": (C.c_int, [vp, vp, vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -391,3 +395,24 @@ def lift_batch_autotune(b: int, iters: int) -> int:
     t = C.c_int()
     _check(load().lift_batch_autotune(C.c_void_p(b), iters, C.byref(t)), "lift_batch_autotune")
     return t.value
+
+
+# ---------------------------------------------------------------------------
+# Differentiable unrolled solve
+# ---------------------------------------------------------------------------
+def lift_set_params(h: int, lam: float, alpha: float, nu: float) -> None:
+    _check(load().lift_set_params(C.c_void_p(h), lam, alpha, nu), "lift_set_params")
+
+
+def lift_unrolled_forward(h: int, iters: int, checkpoint_every: int) -> None:
+    _check(load().lift_unrolled_forward(C.c_void_p(h), iters, checkpoint_every),
+           "lift_unrolled_forward")
+
+
+def lift_unrolled_backward(h: int, grad_u, grad_f=None) -> tuple[float, float, float]:
+    """grad_u, grad_f: device tensors (H*W float32); returns dL/d(lambda, alpha, nu)."""
+    out = (C.c_double * 3)()
+    gf = C.c_void_p(grad_f.data_ptr()) if grad_f is not None else C.c_void_p(0)
+    _check(load().lift_unrolled_backward(C.c_void_p(h), C.c_void_p(grad_u.data_ptr()), gf, out),
+           "lift_unrolled_backward")
+    return out[0], out[1], out[2]

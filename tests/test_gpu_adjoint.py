@@ -1,0 +1,144 @@
+"""The hand-written reverse pass of the unrolled solve (adjoint.cu) against
+the oracle's FP64 reverse pass, checkpoint invariance, the autograd.Function,
+and a first-order Taylor check at the 256x256, L=16, 500-iteration size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_01383_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _require_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def _solver(kind, f, L, lam, alpha, nu, theta=1.0):
+    from paper_1512_01383_gb300 import lift as G
+    H, W = f.shape
+    return G.Solver(kind, H, W, L, 0.0, 1.0, lam, alpha, nu, f=torch.from_numpy(f).cuda(),
+                    step_balance=theta)
+
+
+def _gpu_grads(s, iters, every, clean):
+    from paper_1512_01383_gb300 import lift as G
+    G.lift_unrolled_forward(s.h, iters, every)
+    u = torch.empty((s.H, s.W), device="cuda")
+    G.lift_unlift(s.h, u)
+    cl = torch.from_numpy(clean.astype(np.float32)).cuda()
+    gu = (2.0 * (u - cl)).contiguous()
+    gf = torch.empty_like(u)
+    sc = G.lift_unrolled_backward(s.h, gu, gf)
+    return u.cpu().numpy(), gf.cpu().numpy(), np.array(sc)
+
+
+@pytest.mark.parametrize("kind,L,lam,alpha,nu,theta", [
+    (1, 5, 0.25, 25.0, 0.1, 1.0),
+    (0, 4, 0.2, 1.5, 0.0, 1.0),
+    (1, 9, 0.3, 20.0, 0.08, 1.0),
+    (1, 5, 0.25, 25.0, 0.1, 16.0),
+])
+def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta):
+    _require_gpu()
+    H, W, iters = 11, 9, 30
+    noisy, clean = synth.voronoi_ramps(H, W, 81 + L, cells=4)
+    f = synth.as_f32(noisy)
+    with _solver(kind, f, L, lam, alpha, nu, theta) as s:
+        u, gf, gs = _gpu_grads(s, iters, 7, clean)
+    P = O.Problem(O.TRUNC if kind == 1 else O.QUAD, H, W, L, 0.0, 1.0, lam=lam, alpha=alpha,
+                  nu=nu, f=f.astype(np.float64), theta=theta)
+    X = O.State(P)
+    O.pdhg(P, X, iters)
+    uo = O.unlift(P, X.u)
+    assert np.abs(u.reshape(-1) - uo).max() <= 1e-4
+    gfo, gso = O.unrolled_grad(P, iters, 2.0 * (uo - clean.reshape(-1)))
+    scale = np.abs(gfo).max()
+    assert scale > 1e-3
+    assert np.abs(gf.reshape(-1) - gfo).max() <= 2e-3 * scale
+    # the unrolled map is piecewise smooth: where an FP32 and an FP64 branch
+    # choice differ near a region boundary the one-sided derivatives differ,
+    # so the scalar sums over all records get a 1 % tolerance
+    for g, o in zip(gs, gso):
+        assert abs(g - o) <= 1e-2 * max(abs(o), 1e-2), (gs, gso)
+
+
+def test_checkpoint_spacing_does_not_change_gradients():
+    _require_gpu()
+    H, W, L, iters = 14, 12, 6, 40
+    noisy, clean = synth.voronoi_ramps(H, W, 91)
+    f = synth.as_f32(noisy)
+    res = []
+    with _solver(1, f, L, 0.25, 25.0, 0.1) as s:
+        for every in (1, 7, 40):
+            res.append(_gpu_grads(s, iters, every, clean))
+    for r in res[1:]:
+        np.testing.assert_array_equal(r[0], res[0][0])
+        np.testing.assert_array_equal(r[1], res[0][1])
+        np.testing.assert_array_equal(r[2], res[0][2])
+
+
+def test_autograd_function():
+    _require_gpu()
+    from paper_1512_01383_gb300.autograd import unrolled_solve
+    H, W, L, iters = 12, 10, 5, 25
+    noisy, clean = synth.voronoi_ramps(H, W, 95)
+    f = torch.from_numpy(synth.as_f32(noisy)).cuda().requires_grad_(True)
+    lam = torch.tensor(0.25, dtype=torch.float64, requires_grad=True)
+    al = torch.tensor(25.0, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    with _solver(1, synth.as_f32(noisy), L, 0.25, 25.0, 0.1) as s:
+        u = unrolled_solve(f, lam, al, nu, s, iters, 5)
+        loss = ((u - torch.from_numpy(clean.astype(np.float32)).cuda()) ** 2).sum()
+        loss.backward()
+        u2, gf2, gs2 = _gpu_grads(s, iters, 5, clean)
+    np.testing.assert_allclose(u.detach().cpu().numpy(), u2)
+    np.testing.assert_allclose(f.grad.cpu().numpy(), gf2)
+    np.testing.assert_allclose([lam.grad.item(), al.grad.item(), nu.grad.item()], gs2)
+
+
+def test_full_size_taylor_check():
+    """256x256, L=16, 500 unrolled iterations, checkpoints every 50: the
+    gradient is finite, equals that of a single-segment reverse pass, and
+    predicts the change of the loss when single pixels of f move (FP32
+    central differences, step 1e-3; a move of one pixel leaves the rounding
+    of all distant pixels unchanged, so the quotient is not drowned in the
+    loss's rounding noise as a move of every pixel would be)."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    H = W = 256
+    L, iters = 16, 500
+    noisy, clean = synth.voronoi_ramps(H, W, synth.BASE_SEED + 4)
+    f = synth.as_f32(noisy)
+    s = G.Solver(1, H, W, L, 0.0, 1.0, 0.25, 25.0, 0.1, f=torch.from_numpy(f).cuda())
+    try:
+        u, gf, gs = _gpu_grads(s, iters, 50, clean)
+        assert np.all(np.isfinite(gf)) and np.all(np.isfinite(gs))
+        u1, gf1, gs1 = _gpu_grads(s, iters, 500, clean)
+        np.testing.assert_array_equal(gf, gf1)
+        np.testing.assert_array_equal(gs, gs1)
+
+        def loss_at(fv):
+            G.lift_set_data(s.h, torch.from_numpy(fv).cuda())
+            G.lift_unrolled_forward(s.h, iters, 50)
+            return float(((s.unlift().astype(np.float64) - clean) ** 2).sum())
+
+        # pixels whose gradient is well above the rounding floor; a pixel
+        # passes if either step (1e-3 or 3e-4) stays clear of the map's kinks
+        order = np.argsort(-np.abs(gf).reshape(-1))
+        rel = []
+        for j in order[:40:5]:
+            e = np.zeros_like(f)
+            e.reshape(-1)[j] = 1.0
+            pred = float(gf.reshape(-1)[j])
+            best = np.inf
+            for eps in (1e-3, 3e-4):
+                fd = (loss_at(f + eps * e) - loss_at(f - eps * e)) / (2 * eps)
+                best = min(best, abs(fd - pred) / abs(pred))
+            rel.append(best)
+        rel = np.array(rel)
+        assert np.median(rel) <= 0.05 and (rel <= 0.1).sum() >= 6, rel
+    finally:
+        s.close()
