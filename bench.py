@@ -204,6 +204,81 @@ def run_batch(G, torch, stream, dev, n=64, smin=128, smax=1024, iters=100, reps=
             "ms_per_100_iters": ms_batch}
 
 
+def time_iters(G, torch, solver, iters, stream):
+    """Milliseconds for `iters` iterations of a solver on `stream` (events)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver.iterate(3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.iterate(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_rof64(G, torch, stream, dev):
+    """ROF denoising, 64x64 blobs + noise, L=2: 2000 iterations (latency-bound:
+    reported in microseconds per iteration), and the time to relative gap 1e-5."""
+    from paper_1512_01383_gb300 import synth
+    f = torch.from_numpy(synth.as_f32(synth.gaussian_blobs(64, 64, synth.BASE_SEED))).to(dev)
+    with G.Solver(G.LIFT_QUAD, 64, 64, 2, 0.0, 1.0, 0.2, 1.0, 0.0, f=f,
+                  stream=stream.cuda_stream, check_every=100) as s:
+        ms = time_iters(G, torch, s, 2000, stream)
+        s.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, n = s.solve(100000, 1e-5)
+        dt = time.perf_counter() - t0
+    return {"us_per_iter": 1e3 * ms / 2000, "ms_2000_iters": ms,
+            "time_to_gap_1e-5": {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt}}
+
+
+def run_stereo(G, torch, stream, dev):
+    """Stereo-style PL matching cost, 640x480, 65 integer disparities,
+    lambda=0.05, L=8,16,32: throughput of 200 iterations per L."""
+    from paper_1512_01383_gb300 import synth
+    cost = synth.as_f32(synth.stereo_cost(480, 640, synth.BASE_SEED + 3, ndisp=65)[0])
+    cd = torch.from_numpy(cost).to(dev)
+    out = {}
+    for Lx in (8, 16, 32):
+        with G.Solver(G.LIFT_PL_SAMPLED, 480, 640, Lx, 0.0, 64.0, 0.05, cost=cd,
+                      sample_min=0.0, sample_max=64.0, stream=stream.cuda_stream) as s:
+            ms = time_iters(G, torch, s, 200, stream)
+        out[f"L{Lx}"] = {"value": 480 * 640 * (Lx - 1) * 200 / (ms * 1e-3) / 1e9, "unit": UNIT,
+                         "ms_per_iter": ms / 200}
+    return out
+
+
+def run_differentiable(G, torch, stream, dev, iters=500, every=50):
+    """Unrolled solve for differentiation: 256x256 truncated quadratic, L=16,
+    500 iterations, checkpoints every 50; forward (checkpointed) and the
+    hand-written reverse pass."""
+    from paper_1512_01383_gb300 import synth
+    noisy, clean = synth.voronoi_ramps(256, 256, synth.BASE_SEED + 4)
+    f = torch.from_numpy(synth.as_f32(noisy)).to(dev)
+    cl = torch.from_numpy(clean.astype(np.float32)).to(dev)
+    with G.Solver(G.LIFT_TRUNC_QUAD, 256, 256, 16, 0.0, 1.0, 0.25, 25.0, 0.1, f=f,
+                  stream=stream.cuda_stream) as s:
+        u = torch.empty((256, 256), device=dev)
+        gf = torch.empty_like(u)
+        res = []
+        for _ in range(3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record(stream)
+            G.lift_unrolled_forward(s.h, iters, every)
+            G.lift_unlift(s.h, u)
+            e1.record(stream)
+            gu = (2.0 * (u - cl)).contiguous()
+            G.lift_unrolled_backward(s.h, gu, gf)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            res.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    fwd, bwd = min(r[0] for r in res), min(r[1] for r in res)
+    return {"forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "forward_value": 256 * 256 * 15 * iters / (fwd * 1e-3) / 1e9, "unit": UNIT}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -241,6 +316,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the ROF, stereo and differentiable sections")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -352,6 +429,12 @@ def main():
                 ttg[f"L{Lx}"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
                                  "rel_gap": s2.gap(), "theta": float((Lx - 1) ** 2)}
 
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["rof_64x64_L2"] = run_rof64(G, torch, stream, dev)
+        extra["stereo_640x480"] = run_stereo(G, torch, stream, dev)
+        extra["differentiable_256_L16"] = run_differentiable(G, torch, stream, dev)
+
     batch = None
     if not args.no_batch and rank == 0:
         batch = run_batch(G, torch, stream, dev)
@@ -359,7 +442,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        side, iters = 96, 50
+        side, iters = 192, 60
         v, dt = cpu_sample(f, side, iters)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{side}x{side} crop, L={L}, {iters} iterations + energy + unlift ({dt:.1f} s)"}
@@ -388,6 +471,7 @@ def main():
             "clocks": clk.summary(),
             "time_to_gap_1e-5": ttg or None,
             "batch": batch,
+            "other_configs": extra or None,
             "final_energy": {"primal": energy_buf[-1][0], "dual": energy_buf[-1][1],
                              "nonconvex": energy_buf[-1][2]},
         }
