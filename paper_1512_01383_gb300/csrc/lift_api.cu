@@ -172,6 +172,7 @@ void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<
     P.gmin = static_cast<float>(spec->gamma_min);
     P.lam = static_cast<float>(spec->lambda);
     P.alpha = static_cast<float>(spec->alpha);
+    P.inv_alpha = spec->alpha > 0.0 ? static_cast<float>(1.0 / spec->alpha) : 0.0f;
     P.nu = static_cast<float>(spec->nu);
     P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
     P.tau_u = static_cast<float>(0.2 * th);
@@ -897,6 +898,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
     h->P.lam = static_cast<float>(lambda);
     if (h->kind != LIFT_PL_SAMPLED) {
         h->P.alpha = static_cast<float>(alpha);
+        h->P.inv_alpha = static_cast<float>(1.0 / alpha);
         h->P.nu = static_cast<float>(nu);
         h->P.wtrunc = h->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(nu / alpha)) : 0.0f;
     }

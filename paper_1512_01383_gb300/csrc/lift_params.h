@@ -21,6 +21,7 @@ struct LiftParams {
     float inv_delta;         // 1/Delta
     float gmin;              // gamma_1
     float lam, alpha, nu;    // TV weight, data-term parameters
+    float inv_alpha;         // 1/alpha (quadratic kinds)
     float wtrunc;            // sqrt(nu/alpha): half-width of the parabola
     float tau_u, sigma_q, sigma_p;
     const float4 *icst;      // per interval {gamma_i, tau_s_i, sigma_vz_i, lambda*Delta}

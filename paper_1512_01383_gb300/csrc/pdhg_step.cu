@@ -69,13 +69,21 @@ __device__ __forceinline__ SegScan block_segmented_scan(float val, int seg, int 
     __syncthreads();
     SegScan r{0.0f, 0.0f};
     if (!active) return r;
-    // segments that began in an earlier warp carry that warp's in-warp total
+    // a segment (k <= 64 records) spans at most three warps: add the in-warp
+    // totals of the earlier warps it covers, in straight-line code
+    const int sw = seg >> 5;
     float carry = 0.0f;
-    for (int w = seg >> 5; w < warp; ++w) carry += s_last[w];
+    if (sw < warp) {
+        carry = s_last[warp - 1];
+        if (sw < warp - 1) carry += s_last[warp - 2];
+    }
     r.incl = x + carry;
     const int e = seg + k - 1, ew = e >> 5;
     float ce = 0.0f;
-    for (int w = seg >> 5; w < ew; ++w) ce += s_last[w];
+    if (sw < ew) {
+        ce = s_last[sw];
+        if (sw + 1 < ew) ce += s_last[sw + 1];
+    }
     r.total = s_in[e] + ce;
     return r;
 }
