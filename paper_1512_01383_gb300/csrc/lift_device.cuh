@@ -116,6 +116,17 @@ __device__ __forceinline__ T qpiece_envelope(const QPieceT<T> &q, T t)
     return 0.5f * q.a * d * d;
 }
 
+// Cube root of x >= 0 from the identity x^(1/3) = 2^(log2(x)/3) on the
+// hardware base-2 logarithm / exponential, refined by one Newton step for
+// r^3 = x (r <- (2r + x/r^2)/3), which squares the relative error of the
+// first estimate.
+__device__ __forceinline__ float cube_root(float x)
+{
+    if (x <= 0.0f) return 0.0f;
+    const float r = exp2f(log2f(x) * (1.0f / 3.0f));
+    return (2.0f * r + x / (r * r)) * (1.0f / 3.0f);
+}
+
 // Largest real root of w^3 + p w - Q = 0 with Q >= 0 (Cardano when one real
 // root, trigonometric form when three); written without cancellation.
 __device__ __forceinline__ float cubic_outer_root(float p, float Q)
@@ -123,7 +134,7 @@ __device__ __forceinline__ float cubic_outer_root(float p, float Q)
     const float p3 = p * (1.0f / 3.0f);
     const float D = 0.25f * Q * Q + p3 * p3 * p3;
     if (D >= 0.0f) {
-        const float u1 = cbrtf(0.5f * Q + sqrtf(D));
+        const float u1 = cube_root(0.5f * Q + sqrtf(D));
         if (u1 == 0.0f) return 0.0f;
         const float u2 = -p3 / u1;
         // u1^3 + u2^3 = Q and u1 u2 = -p/3, so u1 + u2 = Q / (u1^2 - u1 u2 + u2^2)
@@ -254,6 +265,25 @@ __device__ __forceinline__ float piece_conj(const LiftParams &P, int pix, int i,
     return qpiece_conj(q, y);
 }
 
+// rho_i^*(y) of a quadratic-type interval straight from its definition,
+// without building the envelope: for rho = min(alpha (t-f)^2, nu),
+// -min(A,B) = max(-A,-B) gives the larger of the clamped-parabola sup and
+// max(l y, r y) - nu; for rho = alpha/2 (t-f)^2 only the clamped parabola.
+// Branch-free; it lets points that already lie in the epigraph (most of
+// them) skip the envelope and the projection.
+__device__ __forceinline__ float quad_conj_direct(const LiftParams &P, float f, float l, float r,
+                                                  float y)
+{
+    if (P.kind == 1) {
+        const float t = fminf(fmaxf(f + y * (0.5f * P.inv_alpha), l), r);
+        const float d = t - f;
+        return fmaxf(t * y - P.alpha * d * d, fmaxf(l * y, r * y) - P.nu);
+    }
+    const float t = fminf(fmaxf(f + y * P.inv_alpha, l), r);
+    const float d = t - f;
+    return t * y - 0.5f * P.alpha * d * d;
+}
+
 template <int KIND>
 __device__ __forceinline__ void piece_project(const LiftParams &P, int pix, int i, float l,
                                               float y0, float h0, float &yo, float &ho)
@@ -261,6 +291,11 @@ __device__ __forceinline__ void piece_project(const LiftParams &P, int pix, int 
     if (KIND == 2) {
         const int b0 = __ldg(P.bstart + i), n = __ldg(P.bstart + i + 1) - b0 + 1;
         pl_project(P.bpos + b0, P.rhat + (size_t)pix * P.nb + b0, n, y0, h0, yo, ho);
+        return;
+    }
+    if (h0 >= quad_conj_direct(P, __ldg(P.f + pix), l, l + P.delta, y0)) {
+        yo = y0;
+        ho = h0;
         return;
     }
     const QPiece q = make_qpiece(P, pix, l, l + P.delta);
