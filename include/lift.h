@@ -111,7 +111,11 @@ int lift_reset(lift_handle h);
 
 /* lift_iterate: run exactly `iters` >= 0 PDHG iterations (Sec. 4), each a
  * dual step from the extrapolated primal followed by a primal step with
- * extrapolation theta = 1.  Asynchronous: returns after enqueueing. */
+ * extrapolation theta = 1.  Whole check intervals (spec->check_every
+ * iterations) are replayed from a CUDA graph on a private stream of the
+ * handle, ordered after the handle stream's earlier work and before its
+ * later work; the rest is launched directly.  Asynchronous: returns after
+ * enqueueing. */
 int lift_iterate(lift_handle h, int iters);
 
 /* lift_dual_step / lift_primal_step: one half-step each, the two kernels

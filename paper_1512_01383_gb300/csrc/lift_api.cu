@@ -38,6 +38,12 @@ struct lift_ctx {
     int unrolled_iters = 0, ckpt_every = 0, ckpt_count = 0, seg_cap = 0;
     lift::AdjState adj{};
     void *adj_arena = nullptr;
+    // graph replay of whole check intervals (lift_iterate)
+    cudaStream_t gstream = nullptr;     // private stream the graph runs on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 0;
 };
 
 namespace {
@@ -69,6 +75,11 @@ void free_ctx(lift_ctx *h)
     if (h->ckpt) cudaFree(h->ckpt);
     if (h->seg) cudaFree(h->seg);
     if (h->adj_arena) cudaFree(h->adj_arena);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
 }
@@ -312,14 +323,67 @@ int lift_reset(lift_handle h)
     return LIFT_OK;
 }
 
+// Drop the captured check-interval graph (its kernels hold the parameters by
+// value, so any parameter change must re-capture).
+static void drop_iter_graph(lift_handle h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->graph_iters = 0;
+}
+
+static int launch_iters(lift_handle h, cudaStream_t st, int iters)
+{
+    for (int n = 0; n < iters; ++n) {
+        LIFT_CK(lift::launch_dual_step(h->P, h->S, st));
+        LIFT_CK(lift::launch_primal_step(h->P, h->S, st));
+    }
+    return LIFT_OK;
+}
+
+// Capture check_every iterations once on a private stream; later calls replay
+// the graph there, ordered after earlier work of the handle's stream and
+// before later work (events), which removes the per-launch host cost that
+// dominates small problems.
+static int ensure_iter_graph(lift_handle h)
+{
+    if (h->gexec && h->graph_iters == h->check_every) return LIFT_OK;
+    drop_iter_graph(h);
+    if (!h->gstream) {
+        LIFT_CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        LIFT_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        LIFT_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    }
+    LIFT_CK(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_iters(h, h->gstream, h->check_every);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->gstream, &g);
+    if (rc != LIFT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return LIFT_ERR_CUDA;
+    }
+    h->graph = g;
+    LIFT_CK(cudaGraphInstantiate(&h->gexec, g, 0));
+    h->graph_iters = h->check_every;
+    return LIFT_OK;
+}
+
 int lift_iterate(lift_handle h, int iters)
 {
     if (!h || iters < 0) return LIFT_ERR_ARG;
-    for (int n = 0; n < iters; ++n) {
-        LIFT_CK(lift::launch_dual_step(h->P, h->S, h->stream));
-        LIFT_CK(lift::launch_primal_step(h->P, h->S, h->stream));
+    const int reps = iters / h->check_every;
+    if (reps > 0) {
+        int rc = ensure_iter_graph(h);
+        if (rc != LIFT_OK) return rc;
+        LIFT_CK(cudaEventRecord(h->ev_in, h->stream));
+        LIFT_CK(cudaStreamWaitEvent(h->gstream, h->ev_in, 0));
+        for (int r = 0; r < reps; ++r) LIFT_CK(cudaGraphLaunch(h->gexec, h->gstream));
+        LIFT_CK(cudaEventRecord(h->ev_out, h->gstream));
+        LIFT_CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
     }
-    return LIFT_OK;
+    return launch_iters(h, h->stream, iters - reps * h->check_every);
 }
 
 int lift_dual_step(lift_handle h)
@@ -895,6 +959,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
     for (int i = 0; i < h->k; ++i) ic[i].w = static_cast<float>(lambda * h->P.delta);
     LIFT_CK(cudaMemcpyAsync(h->icst, ic.data(), h->k * sizeof(float4), cudaMemcpyHostToDevice, h->stream));
     LIFT_CK(cudaStreamSynchronize(h->stream));
+    drop_iter_graph(h);
     h->P.lam = static_cast<float>(lambda);
     if (h->kind != LIFT_PL_SAMPLED) {
         h->P.alpha = static_cast<float>(alpha);

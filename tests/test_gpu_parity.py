@@ -291,3 +291,27 @@ def test_nan_input_reports_nan():
         with pytest.raises(G.LiftError) as e:
             s.energy()
         assert e.value.code == G.LIFT_ERR_NAN
+
+
+def test_graph_replay_equals_direct_launches():
+    """lift_iterate replays whole check intervals from a CUDA graph; the
+    iterate must equal that of the same half-steps launched one by one."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(1, 23, 19, 6, 951)
+    with gpu_solver(c, check_every=40) as a, gpu_solver(c, check_every=40) as b:
+        a.iterate(130)                     # 3 graph replays + 10 direct iterations
+        for _ in range(130):
+            G.lift_dual_step(b.h)
+            G.lift_primal_step(b.h)
+        sa, sb = a.state(), b.state()
+        for k in sa:
+            np.testing.assert_array_equal(sa[k], sb[k])
+        # parameters are baked into the graph: a change must be picked up
+        G.lift_set_params(a.h, 0.4, 25.0, 0.1)
+        G.lift_set_params(b.h, 0.4, 25.0, 0.1)
+        a.iterate(40)
+        for _ in range(40):
+            G.lift_dual_step(b.h)
+            G.lift_primal_step(b.h)
+        np.testing.assert_array_equal(a.unlift(), b.unlift())
