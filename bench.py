@@ -126,6 +126,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The maximum of a per-rank scalar over all ranks (the job's wall time is
+    the slowest rank's); the value itself when not distributed."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_input(rank: int = 0):
     from paper_1512_01383_gb300 import synth
     f, _ = synth.voronoi_ramps(H, W, SEED + rank)
@@ -244,8 +255,11 @@ def run_stereo(G, torch, stream, dev):
         with G.Solver(G.LIFT_PL_SAMPLED, 480, 640, Lx, 0.0, 64.0, 0.05, cost=cd,
                       sample_min=0.0, sample_max=64.0, stream=stream.cuda_stream) as s:
             ms = time_iters(G, torch, s, 200, stream)
+            s.reset()
+            s.iterate(2000)
+            gap = s.gap()
         out[f"L{Lx}"] = {"value": 480 * 640 * (Lx - 1) * 200 / (ms * 1e-3) / 1e9, "unit": UNIT,
-                         "ms_per_iter": ms / 200}
+                         "ms_per_iter": ms / 200, "rel_gap_after_2000_iters": gap}
     return out
 
 
@@ -365,11 +379,7 @@ def main():
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     units = H * W * K_INT * ITERS_PER_STEP * args.steps * world
     value = units / (ms * 1e-3) / 1e9
 
@@ -409,11 +419,7 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = units / float(tt.item()) / 1e9
+    e2e_value = units / max_over_ranks(time.perf_counter() - t0, dev) / 1e9
 
     # time to relative gap 1e-5 (outside the timed region, per L)
     ttg = {}
