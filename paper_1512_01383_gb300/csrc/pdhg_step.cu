@@ -91,6 +91,47 @@ __device__ __forceinline__ SegScan block_segmented_scan(float val, int seg, int 
 // One tile: floor(THREADS/k) whole pixels of one problem instance, one
 // thread per (pixel, interval) record.  Shared by the single-instance kernels
 // and the batched kernels of lift_batch.cu.
+// The same segmented scan for two independent values per thread (two tiles
+// of the same shape processed by one block), one barrier for both.
+struct SegScan2 {
+    float2 incl, total;
+};
+
+__device__ __forceinline__ SegScan2 block_segmented_scan2(float2 val, int seg, int k, int tid,
+                                                          bool active, float2 *s_in, float2 *s_last)
+{
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wbase = warp << 5;
+    const int start = seg > wbase ? seg - wbase : 0;
+    float2 x = val;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float a = __shfl_up_sync(0xffffffffu, x.x, off);
+        const float b = __shfl_up_sync(0xffffffffu, x.y, off);
+        if (lane - off >= start) { x.x += a; x.y += b; }
+    }
+    s_in[tid] = x;
+    if (lane == 31) s_last[warp] = x;
+    __syncthreads();
+    SegScan2 r{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (!active) return r;
+    const int sw = seg >> 5;
+    float2 carry = make_float2(0.f, 0.f);
+    if (sw < warp) {
+        carry = s_last[warp - 1];
+        if (sw < warp - 1) { carry.x += s_last[warp - 2].x; carry.y += s_last[warp - 2].y; }
+    }
+    r.incl = make_float2(x.x + carry.x, x.y + carry.y);
+    const int e = seg + k - 1, ew = e >> 5;
+    float2 ce = make_float2(0.f, 0.f);
+    if (sw < ew) {
+        ce = s_last[sw];
+        if (sw + 1 < ew) { ce.x += s_last[sw + 1].x; ce.y += s_last[sw + 1].y; }
+    }
+    r.total = make_float2(s_in[e].x + ce.x, s_in[e].y + ce.y);
+    return r;
+}
+
 template <int KIND, int THREADS>
 __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__restrict__ xbar,
                                           float4 *__restrict__ y, float *__restrict__ q,
@@ -195,13 +236,48 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     dual_tile<KIND, kStepThreads>(P, xbar, y, q, blockIdx.x, s_in, s_last);
 }
 
+// Single-instance primal step: each block takes two consecutive tiles and
+// issues the loads of both before the (shared) scan, doubling the bytes in
+// flight per thread; the primal step waits on memory rather than on issue.
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q)
 {
-    __shared__ float s_in[kStepThreads];
-    __shared__ float s_last[kStepThreads / 32];
-    primal_tile<kStepThreads>(P, x, xbar, y, q, blockIdx.x, s_in, s_last);
+    __shared__ float2 s_in[kStepThreads];
+    __shared__ float2 s_last[kStepThreads / 32];
+    const int tid = threadIdx.x;
+    int lp, i;
+    split_thread(P, tid, lp, i);
+    int pix[2]; bool act[2]; size_t o[2]; float4 d[2]; float2 xo[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        pix[u] = (2 * blockIdx.x + u) * P.ppb + lp;
+        act[u] = lp < P.ppb && pix[u] < P.N;
+        o[u] = static_cast<size_t>(pix[u]) * P.k + i;
+        d[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        xo[u] = make_float2(0.f, 0.f);
+        if (act[u]) { d[u] = y[o[u]]; xo[u] = x[o[u]]; }
+    }
+    const SegScan2 sc = block_segmented_scan2(make_float2(d[0].x, d[1].x), lp * P.k, P.k, tid,
+                                              act[0] || act[1], s_in, s_last);
+    const float4 ic = __ldg(P.icst + (lp < P.ppb ? i : 0));
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (!act[u]) continue;
+        const int row = pixel_row(P, pix[u]);
+        const int col = pix[u] - row * P.W;
+        const float qq = q[pix[u]];
+        float dv = 0.0f;
+        if (col + 1 < P.W) dv += d[u].z;
+        if (col > 0) dv -= y[o[u] - P.k].z;
+        if (row + 1 < P.H) dv += d[u].w;
+        if (row > 0) dv -= y[o[u] - static_cast<size_t>(P.W) * P.k].w;
+        const float head = (u == 0 ? sc.incl.x : sc.incl.y) - d[u].x;
+        const float un = fminf(fmaxf(xo[u].x - P.tau_u * (d[u].x - dv), 0.0f), 1.0f);
+        const float sn = xo[u].y - ic.y * (d[u].y - P.delta * qq + P.delta * head - ic.x * d[u].x);
+        x[o[u]] = make_float2(un, sn);
+        xbar[o[u]] = make_float2(2.0f * un - xo[u].x, 2.0f * sn - xo[u].y);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -293,7 +369,8 @@ cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream
 
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
 {
-    primal_step_kernel<<<step_blocks(P), kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q);
+    primal_step_kernel<<<(step_blocks(P) + 1) / 2, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y,
+                                                                        S.q);
     return cudaGetLastError();
 }
 
