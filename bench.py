@@ -434,6 +434,17 @@ def main():
                 dt = time.perf_counter() - t0
                 ttg[f"L{Lx}"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
                                  "rel_gap": s2.gap(), "theta": float((Lx - 1) ** 2)}
+            # the same from theta = 1 with the adaptive balance
+            with G.Solver(G.LIFT_TRUNC_QUAD, H, W, Lx, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
+                          check_every=100, stream=stream.cuda_stream, step_balance=1.0,
+                          adaptive_balance=True) as s2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, n = s2.solve(60000, 1e-5)
+                dt = time.perf_counter() - t0
+                ttg[f"L{Lx}_adaptive"] = {"converged": rc == G.LIFT_OK, "iters": n, "seconds": dt,
+                                          "rel_gap": s2.gap(),
+                                          "final_theta": G.lift_get_balance(s2.h)}
 
     extra = {}
     if not args.no_extra and rank == 0:

@@ -84,6 +84,8 @@ typedef struct lift_spec {
     double step_balance;      /* theta > 0: every primal step x theta, every
                                  dual step / theta (tau*sigma unchanged);
                                  <= 0 means 1, the diagonal preconditioner  */
+    int adaptive_balance;     /* 1: lift_solve re-balances theta at every
+                                 check (see lift_solve); 0: theta fixed     */
 } lift_spec;
 
 typedef struct lift_ctx *lift_handle;
@@ -129,8 +131,18 @@ int lift_primal_step(lift_handle h);
  * max_iters iterations.  rel_gap_tol <= 0 runs max_iters iterations with no
  * check.  *iters_done (may be NULL) receives the count.  Returns
  * LIFT_ERR_NOT_CONVERGED if the tolerance was not met, LIFT_ERR_NAN if an
- * energy became non-finite. */
+ * energy became non-finite.
+ * With spec->adaptive_balance, each check also measures how far the primal
+ * and the dual iterate moved since the previous check, dx^2 = sum |dx|^2/tau
+ * and dy^2 = sum |dy|^2/sigma in the metric of the theta = 1 steps, and moves
+ * theta half-way (geometrically) toward dx/dy: the variable that travels
+ * farther gets the larger steps (the primal-weight update of Applegate et
+ * al.'s PDLP; the paper itself cites adaptive steps of Goldstein and Esser).
+ * lift_get_balance returns the current theta. */
 int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done);
+
+/* lift_get_balance: the current primal/dual step balance theta. */
+int lift_get_balance(lift_handle h, double *theta);
 
 /* lift_energy: evaluate, with FP64 reductions over FP32 per-pixel terms:
  *   primal_relaxed  an upper bound on the relaxed optimum: the relaxed

@@ -8,5 +8,5 @@ computes and which passage of arXiv 1512.01383 it follows.
 from .oracle import (  # noqa: F401
     QUAD, TRUNC, PL, Problem, State, build, conj, lifted_conj, proj_epi, biconj,
     rho, grad, div, steps, pdhg, unlift, monotone_proj, energy, rof_direct,
-    rof_energy, labels, unrolled_grad,
+    rof_energy, labels, unrolled_grad, movement, pdhg_adaptive,
 )

@@ -269,3 +269,37 @@ def unrolled_grad(P: Problem, iters: int, g_u: np.ndarray) -> tuple[np.ndarray, 
     if rc != 0:
         raise RuntimeError(f"oracle unrolled_grad failed ({rc})")
     return gf, gs
+
+
+def movement(P: Problem, X: State, Xp: State) -> tuple[float, float]:
+    """Squared movement of the primal and the dual iterate between two states
+    in the metric of the theta = 1 steps: (sum |dx|^2/tau, sum |dy|^2/sigma)."""
+    base = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
+                   f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=1.0)
+    S = steps(base)
+    dx = (np.sum((X.u - Xp.u) ** 2) / S["tau_u"]
+          + np.sum((X.s - Xp.s) ** 2 / S["tau_s"][None, :]))
+    dy = (np.sum(((X.v - Xp.v) ** 2 + (X.z - Xp.z) ** 2) / S["sigma_vz"][None, :])
+          + np.sum((X.px - Xp.px) ** 2 + (X.py - Xp.py) ** 2) / S["sigma_p"]
+          + np.sum((X.q - Xp.q) ** 2) / S["sigma_q"])
+    return float(dx), float(dy)
+
+
+def pdhg_adaptive(P: Problem, X: State, checks: int, every: int) -> float:
+    """`checks` rounds of `every` iterations; after each round log theta moves
+    a fraction w toward log(dx/dy), dx/dy the ratio of the primal to the dual
+    movement in the theta = 1 metric; w starts at 1/2 and shrinks by 0.95 per
+    round.  Returns the final theta."""
+    th = P.theta if P.theta > 0 else 1.0
+    w = 0.5
+    for _ in range(checks):
+        Pc = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
+                     f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=th)
+        Xp = X.copy(Pc)
+        pdhg(Pc, X, every)
+        dx, dy = movement(Pc, X, Xp)
+        if dx > 0 and dy > 0 and np.isfinite(dx) and np.isfinite(dy):
+            th = float(np.exp((1.0 - w) * np.log(th) + w * np.log(np.sqrt(dx / dy))))
+            th = min(max(th, 1e-4), 1e6)
+            w *= 0.95
+    return th

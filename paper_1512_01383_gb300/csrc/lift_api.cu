@@ -44,6 +44,13 @@ struct lift_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_iters = 0;
+    // adaptive primal/dual balance (lift_solve)
+    lift_spec spec_copy{};              // data pointers cleared; for re-deriving steps
+    double theta = 1.0;
+    double adapt_w = 0.5;               // weight of the next re-balancing step
+    int adaptive = 0;
+    char *prev = nullptr;               // state at the previous check
+    bool prev_valid = false;
 };
 
 namespace {
@@ -80,6 +87,7 @@ void free_ctx(lift_ctx *h)
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->gstream) cudaStreamDestroy(h->gstream);
+    if (h->prev) cudaFree(h->prev);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
 }
@@ -201,6 +209,75 @@ int upload_data(lift_handle h, const float *data, int on_host)
     return LIFT_OK;
 }
 
+// Re-derive the step sizes for a new balance theta (icst and the scalar
+// steps; everything else of the parameters is unchanged).
+int set_theta(lift_handle h, double theta)
+{
+    lift_spec sp = h->spec_copy;
+    sp.step_balance = theta;
+    LiftParams P2;
+    std::vector<float4> ic;
+    make_params(&sp, lift::kStepThreads, P2, ic);
+    LIFT_CK(cudaMemcpyAsync(h->icst, ic.data(), ic.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                            h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));   // ic dies here
+    h->P.tau_u = P2.tau_u;
+    h->P.sigma_q = P2.sigma_q;
+    h->P.sigma_p = P2.sigma_p;
+    h->theta = theta;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->graph_iters = 0;
+    return LIFT_OK;
+}
+
+int save_prev(lift_handle h)
+{
+    const size_t sb = lift_state_bytes(h);
+    if (!h->prev) {
+        const int rc = dev_alloc(reinterpret_cast<void **>(&h->prev), (sb + 255) & ~size_t(255));
+        if (rc != LIFT_OK) return rc;
+    }
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    char *b = h->prev;
+    LIFT_CK(cudaMemcpyAsync(b, h->S.x, Nk * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    LIFT_CK(cudaMemcpyAsync(b + 2 * Nk * sizeof(float2), h->S.y, Nk * sizeof(float4),
+                            cudaMemcpyDeviceToDevice, h->stream));
+    LIFT_CK(cudaMemcpyAsync(b + 2 * Nk * sizeof(float2) + Nk * sizeof(float4), h->S.q,
+                            h->N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    h->prev_valid = true;
+    return LIFT_OK;
+}
+
+// log theta <- (1 - w) log theta + w log(dx/dy), dx, dy the movements since
+// the previous check in the metric of the theta = 1 steps; the weight w starts
+// at 1/2 and shrinks by 0.95 per check, so the steps settle (a decaying
+// adaptation, as in the adaptive primal-dual steps the paper cites).
+int rebalance(lift_handle h)
+{
+    if (!h->prev_valid) return LIFT_OK;
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    LiftState Sp;
+    Sp.x = reinterpret_cast<float2 *>(h->prev);
+    Sp.xbar = nullptr;
+    Sp.y = reinterpret_cast<float4 *>(h->prev + 2 * Nk * sizeof(float2));
+    Sp.q = reinterpret_cast<float *>(h->prev + 2 * Nk * sizeof(float2) + Nk * sizeof(float4));
+    LIFT_CK(lift::launch_movement(h->P, h->S, Sp, static_cast<float>(h->theta), h->partial, h->dout,
+                                  h->stream));
+    LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));
+    const double dx = h->hout[0], dy = h->hout[1];
+    if (!(dx > 0.0) || !(dy > 0.0) || !is_finite(dx) || !is_finite(dy)) return LIFT_OK;
+    const double w = h->adapt_w;
+    double th = exp((1.0 - w) * log(h->theta) + w * 0.5 * log(dx / dy));
+    th = std::min(std::max(th, 1e-4), 1e6);
+    h->adapt_w *= 0.95;
+    return set_theta(h, th);
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,6 +304,11 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     std::vector<float4> ic;
     LiftParams &P = h->P;
     make_params(spec, lift::kStepThreads, P, ic);
+    h->spec_copy = *spec;
+    h->spec_copy.f = nullptr;
+    h->spec_copy.cost = nullptr;
+    h->theta = spec->step_balance > 0.0 ? spec->step_balance : 1.0;
+    h->adaptive = spec->adaptive_balance ? 1 : 0;
 
     std::vector<float> bp;
     std::vector<int> bs;
@@ -320,6 +402,8 @@ int lift_reset(lift_handle h)
     LIFT_CK(cudaMemsetAsync(h->S.xbar, 0, Nk * sizeof(float2), h->stream));
     LIFT_CK(cudaMemsetAsync(h->S.y, 0, Nk * sizeof(float4), h->stream));
     LIFT_CK(cudaMemsetAsync(h->S.q, 0, h->N * sizeof(float), h->stream));
+    h->prev_valid = false;
+    h->adapt_w = 0.5;
     return LIFT_OK;
 }
 
@@ -435,6 +519,10 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
     }
     int done = 0;
     while (done < max_iters) {
+        if (h->adaptive) {
+            const int rc = save_prev(h);
+            if (rc != LIFT_OK) return rc;
+        }
         const int chunk = std::min(h->check_every, max_iters - done);
         int rc = lift_iterate(h, chunk);
         if (rc != LIFT_OK) return rc;
@@ -444,8 +532,19 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
         rc = lift_gap(h, &g);
         if (rc != LIFT_OK) return rc;
         if (g <= rel_gap_tol) return LIFT_OK;
+        if (h->adaptive) {
+            rc = rebalance(h);
+            if (rc != LIFT_OK) return rc;
+        }
     }
     return LIFT_ERR_NOT_CONVERGED;
+}
+
+int lift_get_balance(lift_handle h, double *theta)
+{
+    if (!h || !theta) return LIFT_ERR_ARG;
+    *theta = h->theta;
+    return LIFT_OK;
 }
 
 int lift_unlift(lift_handle h, float *out, int on_host)

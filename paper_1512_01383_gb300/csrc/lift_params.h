@@ -84,6 +84,11 @@ int energy_blocks(const LiftParams &P);
 cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *partial,
                           double *out, cudaStream_t st);
 cudaError_t launch_unlift(const LiftParams &P, const float2 *x, float *out, cudaStream_t st);
+// out[0] = sum |u - u'|^2/tau_u + |s - s'|^2/tau_s, out[1] = sum over the dual
+// records |.|^2/sigma, both in the metric of the theta = 1 steps (the
+// current steps are those of balance theta).
+cudaError_t launch_movement(const LiftParams &P, const LiftState &S, const LiftState &Sprev,
+                            float theta, double *partial, double *out, cudaStream_t st);
 cudaError_t launch_proj_epi(const LiftParams &P, const int *pix, const int *interval,
                             const float *y0, const float *h0, float *y, float *h, int n,
                             cudaStream_t st);

@@ -243,6 +243,64 @@ cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *parti
 }
 
 // ---------------------------------------------------------------------------
+// Movement of the iterate between two checks (adaptive balance), one thread
+// per pixel; the steps of balance theta are converted to those of theta = 1
+// (tau / theta, sigma * theta).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kEnergyThreads)
+movement_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__restrict__ y,
+                const float *__restrict__ q, const float2 *__restrict__ xp,
+                const float4 *__restrict__ yp, const float *__restrict__ qp, float theta,
+                double *__restrict__ partial)
+{
+    const int pix = blockIdx.x * kEnergyThreads + threadIdx.x;
+    double mx = 0.0, my = 0.0;
+    if (pix < P.N) {
+        const size_t o = static_cast<size_t>(pix) * P.k;
+        const float itu = theta / P.tau_u;           // 1 / (tau_u / theta)
+        const float isp = 1.0f / (P.sigma_p * theta);
+        for (int i = 0; i < P.k; ++i) {
+            const float4 ic = P.icst[i];
+            const float2 a = x[o + i], b = xp[o + i];
+            const float du = a.x - b.x, ds = a.y - b.y;
+            mx += static_cast<double>(du * du * itu + ds * ds * (theta / ic.y));
+            const float4 c = y[o + i], e = yp[o + i];
+            const float dv = c.x - e.x, dz = c.y - e.y, dpx = c.z - e.z, dpy = c.w - e.w;
+            my += static_cast<double>((dv * dv + dz * dz) / (ic.z * theta) + (dpx * dpx + dpy * dpy) * isp);
+        }
+        const float dq = q[pix] - qp[pix];
+        my += static_cast<double>(dq * dq / (P.sigma_q * theta));
+    }
+    __shared__ double red[2][kEnergyThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+        mx += __shfl_down_sync(0xffffffffu, mx, off);
+        my += __shfl_down_sync(0xffffffffu, my, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wid] = mx; red[1][wid] = my; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < kEnergyThreads / 32; ++j) { a += red[0][j]; b += red[1][j]; }
+        partial[3 * blockIdx.x + 0] = a;
+        partial[3 * blockIdx.x + 1] = b;
+        partial[3 * blockIdx.x + 2] = 0.0;
+    }
+}
+
+cudaError_t launch_movement(const LiftParams &P, const LiftState &S, const LiftState &Sprev,
+                            float theta, double *partial, double *out, cudaStream_t st)
+{
+    const int nb = energy_blocks(P);
+    movement_kernel<<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.q, Sprev.x, Sprev.y, Sprev.q,
+                                                   theta, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    energy_finish_kernel<<<1, kEnergyThreads, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Unlifting (layer-cake formula, Sec. 3).
 // ---------------------------------------------------------------------------
 __global__ void unlift_kernel(const LiftParams P, const float2 *__restrict__ x,

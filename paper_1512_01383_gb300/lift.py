@@ -30,6 +30,7 @@ EXPORTED = (
     "lift_batch_iterate", "lift_batch_solve", "lift_batch_energy", "lift_batch_unlift",
     "lift_batch_get_state", "lift_batch_autotune",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
+    "lift_get_balance",
 )
 
 
@@ -41,6 +42,7 @@ class lift_spec(C.Structure):
         ("f", C.c_void_p), ("cost", C.c_void_p), ("n_samples", C.c_int),
         ("sample_min", C.c_double), ("sample_max", C.c_double),
         ("data_on_host", C.c_int), ("check_every", C.c_int), ("step_balance", C.c_double),
+        ("adaptive_balance", C.c_int),
     ]
 
 
@@ -94,6 +96,7 @@ def load(path: str = LIB_PATH):
         "lift_set_params": (C.c_int, [vp, C.c_double, C.c_double, C.c_double]),
         "lift_unrolled_forward": (C.c_int, [vp, C.c_int, C.c_int]),
         "lift_unrolled_backward": (C.c_int, [vp, vp, vp, dp]),
+        "lift_get_balance": (C.c_int, [vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -179,6 +182,12 @@ def lift_solve(h: int, max_iters: int, rel_gap_tol: float) -> tuple[int, int]:
     return rc, n.value
 
 
+def lift_get_balance(h: int) -> float:
+    t = C.c_double()
+    _check(load().lift_get_balance(C.c_void_p(h), C.byref(t)), "lift_get_balance")
+    return t.value
+
+
 def lift_energy(h: int) -> tuple[float, float, float]:
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     _check(load().lift_energy(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)), "lift_energy")
@@ -239,7 +248,8 @@ def lift_energy_noalloc(spec: lift_spec, state, out, stream: int | None = None) 
 def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: float,
               lam: float, alpha: float = 1.0, nu: float = 0.0, f=None, cost=None,
               sample_min: float = 0.0, sample_max: float = 1.0,
-              check_every: int = 100, step_balance: float = 1.0) -> lift_spec:
+              check_every: int = 100, step_balance: float = 1.0,
+              adaptive_balance: bool = False) -> lift_spec:
     data = f if kind != LIFT_PL_SAMPLED else cost
     p, on_host = _ptr(data)
     n_samples = 0
@@ -247,7 +257,8 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
         n_samples = int(cost.shape[-1])
     return lift_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu,
                      p if kind != LIFT_PL_SAMPLED else 0, p if kind == LIFT_PL_SAMPLED else 0,
-                     n_samples, sample_min, sample_max, on_host, check_every, step_balance)
+                     n_samples, sample_min, sample_max, on_host, check_every, step_balance,
+                     1 if adaptive_balance else 0)
 
 
 class Solver:
@@ -257,10 +268,10 @@ class Solver:
                  gamma_max: float = 1.0, lam: float = 0.0, alpha: float = 1.0,
                  nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
                  sample_max: float = 1.0, check_every: int = 100, stream: int | None = None,
-                 step_balance: float = 1.0):
+                 step_balance: float = 1.0, adaptive_balance: bool = False):
         self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
         self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
-                              sample_min, sample_max, check_every, step_balance)
+                              sample_min, sample_max, check_every, step_balance, adaptive_balance)
         self._keep = (f, cost)
         self.h = lift_create(self.spec, stream)
         self._keep = None

@@ -315,3 +315,23 @@ def test_graph_replay_equals_direct_launches():
             G.lift_dual_step(b.h)
             G.lift_primal_step(b.h)
         np.testing.assert_array_equal(a.unlift(), b.unlift())
+
+
+@pytest.mark.parametrize("L", [5, 10])
+def test_adaptive_balance_matches_oracle(L):
+    """lift_solve with adaptive_balance re-balances theta at every check from
+    the movement since the previous check; the same rule on the oracle gives
+    the same theta sequence and iterate."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(1, 21, 18, L, 990 + L)
+    P = oracle_problem(c)
+    X = O.State(P)
+    th_o = O.pdhg_adaptive(P, X, 5, 100)
+    with gpu_solver(c, check_every=100, adaptive_balance=True) as s:
+        rc, n = s.solve(500, 1e-15)
+        assert rc == G.LIFT_ERR_NOT_CONVERGED and n == 500
+        th_g = G.lift_get_balance(s.h)
+        ut = s.unlift()
+    assert abs(th_g - th_o) <= 1e-3 * th_o, (th_g, th_o)
+    assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() <= U_TOL

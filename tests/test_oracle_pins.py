@@ -498,3 +498,37 @@ def test_1d_dynamic_programming_bound(seed):
         # converged; the relaxed optimum E* lies in [D, P_hat] and the DP on a
         # grid of step 2.5e-4 overestimates the graph optimum only slightly
         assert E_dp - D < 2e-3
+
+
+def test_adaptive_balance_converges_like_tuned_balance():
+    """The movement-balancing rule, started from theta = 1, reaches a gap
+    within a small factor of the hand-tuned constant balance and far below
+    the plain preconditioner's (truncated quadratic, L = 10)."""
+    f = synth.voronoi_ramps(16, 16, 57)[0]
+
+    def gap_after(theta, adaptive):
+        P = O.Problem(O.TRUNC, 16, 16, 10, 0.0, 1.0, lam=0.25, alpha=25.0, nu=0.1, f=f,
+                      theta=theta)
+        X = O.State(P)
+        if adaptive:
+            O.pdhg_adaptive(P, X, 20, 100)
+        else:
+            O.pdhg(P, X, 2000)
+        Ph, D, _ = O.energy(P, X)
+        assert Ph >= D - 1e-10
+        return (Ph - D) / max(abs(Ph), abs(D), 1.0)
+
+    ga, gt, g1 = gap_after(1.0, True), gap_after(81.0, False), gap_after(1.0, False)
+    assert ga < 0.1 * g1 and ga < 5.0 * gt, (ga, gt, g1)
+
+
+def test_movement_is_weighted_squared_change():
+    P = O.Problem(O.TRUNC, 3, 4, 5, 0.0, 1.0, lam=0.25, alpha=25.0, nu=0.1,
+                  f=synth.voronoi_ramps(3, 4, 58)[0], theta=7.0)
+    X, Y = O.State(P), O.State(P)
+    Y.u[1, 2] = 0.5
+    Y.q[3] = 2.0
+    st = O.steps(O.Problem(O.TRUNC, 3, 4, 5, 0.0, 1.0, lam=0.25, alpha=25.0, nu=0.1, f=P.f))
+    dx, dy = O.movement(P, Y, X)
+    assert dx == pytest.approx(0.25 / st["tau_u"])
+    assert dy == pytest.approx(4.0 / st["sigma_q"])
