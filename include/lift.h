@@ -86,6 +86,10 @@ typedef struct lift_spec {
                                  <= 0 means 1, the diagonal preconditioner  */
     int adaptive_balance;     /* 1: lift_solve re-balances theta at every
                                  check (see lift_solve); 0: theta fixed     */
+    int tv_anisotropic;       /* 0: isotropic TV, |nu|_2 in Phi_{i,j} (K = l2
+                                 balls, Prop. 5); 1: anisotropic |nu|_1
+                                 (K = l-infinity boxes |p_i|_inf <= lambda
+                                 Delta, Sec. 5.3)                          */
 } lift_spec;
 
 typedef struct lift_ctx *lift_handle;

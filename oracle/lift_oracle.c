@@ -59,7 +59,30 @@ typedef struct {
     int ns;                /* number of samples per pixel (PL)             */
     double smin, smax;     /* sample positions smin + j (smax-smin)/(ns-1)  */
     double theta;          /* primal/dual step balance (<= 0 means 1)      */
+    int aniso;             /* 1: phi(nu) = |nu|_1 (anisotropic TV), K is a  */
+                           /*    product of l-infinity boxes; 0: |nu|_2     */
 } orc_problem;
+
+/* The norm phi of the jump direction in Phi_{i,j} (eq. regularizer_single)
+   and the projection onto the dual-norm ball of radius R (Prop. 5 holds for
+   any convex one-homogeneous phi, Sec. 5.3). */
+static double tv_norm(int aniso, double a, double b)
+{
+    return aniso ? fabs(a) + fabs(b) : sqrt(a * a + b * b);
+}
+
+static void tv_project(int aniso, double R, double *a, double *b)
+{
+    if (aniso) {
+        *a = *a > R ? R : (*a < -R ? -R : *a);
+        *b = *b > R ? R : (*b < -R ? -R : *b);
+        return;
+    }
+    double nrm = sqrt(*a * *a + *b * *b);
+    double sc = nrm > R ? (nrm > 0.0 ? R / nrm : 0.0) : 1.0;
+    *a *= sc;
+    *b *= sc;
+}
 
 /* PDHG state; all arrays caller-allocated, index [pixel*k + i]. */
 typedef struct {
@@ -368,10 +391,9 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
                 double d = gam(P, i + 1) - gam(P, i);
                 double ax = px[i] + S.sigma_p * gx[pix * k + i];
                 double ay = py[i] + S.sigma_p * gy[pix * k + i];
-                double nrm = sqrt(ax * ax + ay * ay), R = P->lam * d;
-                double sc = nrm > R ? (nrm > 0.0 ? R / nrm : 0.0) : 1.0;
-                px[i] = ax * sc;
-                py[i] = ay * sc;
+                tv_project(P->aniso, P->lam * d, &ax, &ay);
+                px[i] = ax;
+                py[i] = ay;
             }
             /* data duals: ascent on v, z, q */
             double tot = 0.0;
@@ -521,7 +543,7 @@ void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
     double tv = 0.0;
     for (size_t o = 0; o < Nk; ++o) {
         int i = (int)(o % k);
-        tv += (gam(P, i + 1) - gam(P, i)) * sqrt(gx[o] * gx[o] + gy[o] * gy[o]);
+        tv += (gam(P, i + 1) - gam(P, i)) * tv_norm(P->aniso, gx[o], gy[o]);
     }
     Pd += P->lam * tv;
 
@@ -533,7 +555,7 @@ void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
             size_t pix = (size_t)y * W + x;
             double ax = x + 1 < W ? ut[pix + 1] - ut[pix] : 0.0;
             double ay = y + 1 < H ? ut[pix + W] - ut[pix] : 0.0;
-            E += orc_rho(P, (int)pix, ut[pix]) + P->lam * sqrt(ax * ax + ay * ay);
+            E += orc_rho(P, (int)pix, ut[pix]) + P->lam * tv_norm(P->aniso, ax, ay);
         }
 
     *Phat = Pd;
@@ -550,6 +572,8 @@ void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
 /* and the tightness of the relaxation for convex data terms.               */
 /* Returns the final primal-dual gap.                                        */
 /* ------------------------------------------------------------------------ */
+static int g_rof_aniso = 0;   /* set by orc_rof_direct_aniso for its duration */
+
 static double rof_primal(int H, int W, const double *u, const double *f,
                          double alpha, double lam)
 {
@@ -559,7 +583,7 @@ static double rof_primal(int H, int W, const double *u, const double *f,
             size_t o = (size_t)y * W + x;
             double ax = x + 1 < W ? u[o + 1] - u[o] : 0.0;
             double ay = y + 1 < H ? u[o + W] - u[o] : 0.0;
-            e += 0.5 * alpha * (u[o] - f[o]) * (u[o] - f[o]) + lam * sqrt(ax * ax + ay * ay);
+            e += 0.5 * alpha * (u[o] - f[o]) * (u[o] - f[o]) + lam * tv_norm(g_rof_aniso, ax, ay);
         }
     return e;
 }
@@ -580,10 +604,9 @@ double orc_rof_direct(int H, int W, const double *f, double alpha, double lam,
         orc_grad(H, W, 1, ub, gx, gy);
         for (size_t o = 0; o < N; ++o) {
             double ax = px[o] + sigma * gx[o], ay = py[o] + sigma * gy[o];
-            double nrm = sqrt(ax * ax + ay * ay);
-            double sc = nrm > lam ? (nrm > 0.0 ? lam / nrm : 0.0) : 1.0;
-            px[o] = ax * sc;
-            py[o] = ay * sc;
+            tv_project(g_rof_aniso, lam, &ax, &ay);
+            px[o] = ax;
+            py[o] = ay;
         }
         orc_div(H, W, 1, px, py, dv);
         double theta = 1.0 / sqrt(1.0 + 2.0 * alpha * tau);
@@ -613,6 +636,25 @@ double orc_rof_energy(int H, int W, const double *u, const double *f,
                       double alpha, double lam)
 {
     return rof_primal(H, W, u, f, alpha, lam);
+}
+
+/* The same two functions with the anisotropic TV |grad u|_1. */
+double orc_rof_direct_aniso(int H, int W, const double *f, double alpha, double lam,
+                            double lo, double hi, int iters, double *u)
+{
+    g_rof_aniso = 1;
+    double g = orc_rof_direct(H, W, f, alpha, lam, lo, hi, iters, u);
+    g_rof_aniso = 0;
+    return g;
+}
+
+double orc_rof_energy_aniso(int H, int W, const double *u, const double *f,
+                            double alpha, double lam)
+{
+    g_rof_aniso = 1;
+    double e = rof_primal(H, W, u, f, alpha, lam);
+    g_rof_aniso = 0;
+    return e;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -742,7 +784,12 @@ int orc_unrolled_grad(const orc_problem *P, int iters, const double *g_u, double
                     double nrm = sqrt(a0 * a0 + a1 * a1), R = P->lam * d;
                     double ap0 = ay[4 * o + 2], ap1 = ay[4 * o + 3];
                     double aa0 = ap0, aa1 = ap1;
-                    if (nrm > R) {
+                    if (P->aniso) {
+                        /* componentwise clamp to [-R, R]: identity inside,
+                           the bound (dR/dlambda = Delta) outside */
+                        if (fabs(a0) > R) { grad_scal[0] += d * (a0 > 0 ? 1.0 : -1.0) * ap0; aa0 = 0.0; }
+                        if (fabs(a1) > R) { grad_scal[0] += d * (a1 > 0 ? 1.0 : -1.0) * ap1; aa1 = 0.0; }
+                    } else if (nrm > R) {
                         double h0 = a0 / nrm, h1 = a1 / nrm, dot = h0 * ap0 + h1 * ap1;
                         aa0 = (R / nrm) * (ap0 - h0 * dot);
                         aa1 = (R / nrm) * (ap1 - h1 * dot);

@@ -32,6 +32,7 @@ class _Problem(C.Structure):
         ("alpha", C.c_double), ("nu", C.c_double),
         ("f", _dp), ("cost", _dp), ("ns", C.c_int),
         ("smin", C.c_double), ("smax", C.c_double), ("theta", C.c_double),
+        ("aniso", C.c_int),
     ]
 
 
@@ -84,6 +85,12 @@ def _load():
                                        C.c_double, C.c_double, C.c_int, _dp]
         lib.orc_unrolled_grad.restype = C.c_int
         lib.orc_unrolled_grad.argtypes = [P, C.c_int, _dp, _dp, _dp]
+        for nm in ("orc_rof_direct_aniso",):
+            getattr(lib, nm).restype = C.c_double
+            getattr(lib, nm).argtypes = [C.c_int, C.c_int, _dp, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_int, _dp]
+        lib.orc_rof_energy_aniso.restype = C.c_double
+        lib.orc_rof_energy_aniso.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double]
         lib.orc_rof_energy.restype = C.c_double
         lib.orc_rof_energy.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_double, C.c_double]
         _lib = lib
@@ -120,6 +127,7 @@ class Problem:
     smin: float = 0.0
     smax: float = 1.0
     theta: float = 1.0
+    aniso: int = 0
     _c: _Problem = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -130,7 +138,7 @@ class Problem:
         ns = 0 if self.cost is None else self.cost.shape[1]
         self._c = _Problem(self.kind, self.H, self.W, self.L, self.gmin, self.gmax, self.lam,
                            self.alpha, self.nu, _ptr(self.f), _ptr(self.cost), ns,
-                           self.smin, self.smax, self.theta)
+                           self.smin, self.smax, self.theta, self.aniso)
 
     @property
     def k(self) -> int:
@@ -244,20 +252,24 @@ def energy(P: Problem, X: State) -> tuple[float, float, float]:
 
 
 def rof_direct(f: np.ndarray, alpha: float, lam: float, lo: float, hi: float,
-               iters: int) -> tuple[np.ndarray, float]:
-    """Unlifted box-constrained ROF by accelerated primal-dual; (u, gap)."""
+               iters: int, aniso: bool = False) -> tuple[np.ndarray, float]:
+    """Unlifted box-constrained ROF by accelerated primal-dual; (u, gap).
+    aniso: |grad u|_1 instead of |grad u|_2."""
     H, W = f.shape
     fd = np.ascontiguousarray(f, dtype=np.float64)
     u = np.empty_like(fd)
-    gap = _load().orc_rof_direct(H, W, _ptr(fd), alpha, lam, lo, hi, iters, _ptr(u))
+    fn = _load().orc_rof_direct_aniso if aniso else _load().orc_rof_direct
+    gap = fn(H, W, _ptr(fd), alpha, lam, lo, hi, iters, _ptr(u))
     return u, gap
 
 
-def rof_energy(u: np.ndarray, f: np.ndarray, alpha: float, lam: float) -> float:
+def rof_energy(u: np.ndarray, f: np.ndarray, alpha: float, lam: float,
+               aniso: bool = False) -> float:
     H, W = f.shape
     u = np.ascontiguousarray(u, dtype=np.float64)
     fd = np.ascontiguousarray(f, dtype=np.float64)
-    return _load().orc_rof_energy(H, W, _ptr(u), _ptr(fd), alpha, lam)
+    fn = _load().orc_rof_energy_aniso if aniso else _load().orc_rof_energy
+    return fn(H, W, _ptr(u), _ptr(fd), alpha, lam)
 
 
 def unrolled_grad(P: Problem, iters: int, g_u: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
@@ -275,7 +287,7 @@ def movement(P: Problem, X: State, Xp: State) -> tuple[float, float]:
     """Squared movement of the primal and the dual iterate between two states
     in the metric of the theta = 1 steps: (sum |dx|^2/tau, sum |dy|^2/sigma)."""
     base = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
-                   f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=1.0)
+                   f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=1.0, aniso=P.aniso)
     S = steps(base)
     dx = (np.sum((X.u - Xp.u) ** 2) / S["tau_u"]
           + np.sum((X.s - Xp.s) ** 2 / S["tau_s"][None, :]))
@@ -294,7 +306,7 @@ def pdhg_adaptive(P: Problem, X: State, checks: int, every: int) -> float:
     w = 0.5
     for _ in range(checks):
         Pc = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
-                     f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=th)
+                     f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=th, aniso=P.aniso)
         Xp = X.copy(Pc)
         pdhg(Pc, X, every)
         dx, dy = movement(Pc, X, Xp)

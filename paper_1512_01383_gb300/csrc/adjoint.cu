@@ -166,7 +166,11 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
         const float py = d.w + P.sigma_p * gy;
         const float n2 = px * px + py * py;
         adj_a = make_float2(a.z, a.w);
-        if (n2 > ic.w * ic.w) {
+        if (P.aniso) {
+            // componentwise clamp to [-R, R]: identity inside, the bound outside
+            if (fabsf(px) > ic.w) { gl += static_cast<double>(P.delta * copysignf(1.0f, px) * a.z); adj_a.x = 0.0f; }
+            if (fabsf(py) > ic.w) { gl += static_cast<double>(P.delta * copysignf(1.0f, py) * a.w); adj_a.y = 0.0f; }
+        } else if (n2 > ic.w * ic.w) {
             // p' = R a/|a|: J = (R/|a|)(I - a a^T/|a|^2), dp'/dR = a/|a|, R = lambda Delta
             const float inv = rsqrtf(n2);
             const float hx = px * inv, hy = py * inv;

@@ -105,6 +105,7 @@ int validate(const lift_spec *s)
         return LIFT_ERR_SPEC;
     if (!is_finite(s->lambda) || s->lambda < 0.0) return LIFT_ERR_SPEC;
     if (!is_finite(s->step_balance)) return LIFT_ERR_SPEC;
+    if (s->tv_anisotropic != 0 && s->tv_anisotropic != 1) return LIFT_ERR_SPEC;
     if (s->kind == LIFT_QUAD || s->kind == LIFT_TRUNC_QUAD) {
         if (!s->f) return LIFT_ERR_SPEC;
         if (!is_finite(s->alpha) || !(s->alpha > 0.0)) return LIFT_ERR_SPEC;
@@ -175,6 +176,7 @@ void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<
     P = LiftParams{};
     P.H = spec->H; P.W = spec->W; P.k = k; P.N = spec->H * spec->W;
     P.kind = spec->kind;
+    P.aniso = spec->tv_anisotropic ? 1 : 0;
     P.ppb = threads / k;
     P.inv_k = 1.0f / static_cast<float>(k);
     P.delta = static_cast<float>(d);

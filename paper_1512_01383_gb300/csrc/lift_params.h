@@ -13,6 +13,7 @@ namespace lift {
 struct LiftParams {
     int H, W, k, N;          // image size, intervals, pixels
     int kind;                // 0 quadratic, 1 truncated quadratic, 2 PL
+    int aniso;               // 1: anisotropic TV (box projection of p_i)
     int ppb;                 // pixels per 256-thread tile in the step kernels
     float inv_k;             // 1/k, for the exact thread -> (pixel, interval) split
     unsigned long long wmul; // row = (pix * wmul) >> wshift, exact for pix < 2^31

@@ -162,11 +162,16 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
     const float gy = row + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
     float px = d.z + P.sigma_p * gx;
     float py = d.w + P.sigma_p * gy;
-    const float n2 = px * px + py * py;
-    if (n2 > ic.w * ic.w) {
-        const float sc2 = ic.w * rsqrtf(n2);
-        px *= sc2;
-        py *= sc2;
+    if (P.aniso) {                              // l-infinity box (anisotropic TV)
+        px = fminf(fmaxf(px, -ic.w), ic.w);
+        py = fminf(fmaxf(py, -ic.w), ic.w);
+    } else {                                    // l2 ball (isotropic TV)
+        const float n2 = px * px + py * py;
+        if (n2 > ic.w * ic.w) {
+            const float sc2 = ic.w * rsqrtf(n2);
+            px *= sc2;
+            py *= sc2;
+        }
     }
 
     // data duals: sum of sbar over the pixel's later intervals = total - inclusive

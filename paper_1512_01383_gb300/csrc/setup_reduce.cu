@@ -167,7 +167,8 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
             }
             const float ax = hr ? wr[i] - w[i] : 0.0f;
             const float ay = hd ? wd[i] - w[i] : 0.0f;
-            tv += static_cast<double>(P.delta * sqrtf(ax * ax + ay * ay));
+            tv += static_cast<double>(P.delta * (P.aniso ? fabsf(ax) + fabsf(ay)
+                                                         : sqrtf(ax * ax + ay * ay)));
             Snext = Si;
         }
         eP = dat + static_cast<double>(P.lam) * tv;
@@ -177,7 +178,8 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
         const float ax = hr ? unlift_pixel(x + o + sx, k, P.gmin, P.delta) - ut : 0.0f;
         const float ay = hd ? unlift_pixel(x + o + sy, k, P.gmin, P.delta) - ut : 0.0f;
         eE = static_cast<double>(data_rho(P, pix, ut)) +
-             static_cast<double>(P.lam) * static_cast<double>(sqrtf(ax * ax + ay * ay));
+             static_cast<double>(P.lam) *
+                 static_cast<double>(P.aniso ? fabsf(ax) + fabsf(ay) : sqrtf(ax * ax + ay * ay));
     }
 
     // block reduction: warp shuffles, then one value per warp
@@ -431,6 +433,7 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
     const int k = spec->L - 1;
     P.H = spec->H; P.W = spec->W; P.k = k; P.N = static_cast<int>(npix);
     P.kind = spec->kind;
+    P.aniso = spec->tv_anisotropic ? 1 : 0;
     P.delta = static_cast<float>((spec->gamma_max - spec->gamma_min) / k);
     P.gmin = static_cast<float>(spec->gamma_min);
     P.lam = static_cast<float>(spec->lambda);

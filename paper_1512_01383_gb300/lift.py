@@ -42,7 +42,7 @@ class lift_spec(C.Structure):
         ("f", C.c_void_p), ("cost", C.c_void_p), ("n_samples", C.c_int),
         ("sample_min", C.c_double), ("sample_max", C.c_double),
         ("data_on_host", C.c_int), ("check_every", C.c_int), ("step_balance", C.c_double),
-        ("adaptive_balance", C.c_int),
+        ("adaptive_balance", C.c_int), ("tv_anisotropic", C.c_int),
     ]
 
 
@@ -249,7 +249,7 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
               lam: float, alpha: float = 1.0, nu: float = 0.0, f=None, cost=None,
               sample_min: float = 0.0, sample_max: float = 1.0,
               check_every: int = 100, step_balance: float = 1.0,
-              adaptive_balance: bool = False) -> lift_spec:
+              adaptive_balance: bool = False, anisotropic: bool = False) -> lift_spec:
     data = f if kind != LIFT_PL_SAMPLED else cost
     p, on_host = _ptr(data)
     n_samples = 0
@@ -258,7 +258,7 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
     return lift_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu,
                      p if kind != LIFT_PL_SAMPLED else 0, p if kind == LIFT_PL_SAMPLED else 0,
                      n_samples, sample_min, sample_max, on_host, check_every, step_balance,
-                     1 if adaptive_balance else 0)
+                     1 if adaptive_balance else 0, 1 if anisotropic else 0)
 
 
 class Solver:
@@ -268,10 +268,12 @@ class Solver:
                  gamma_max: float = 1.0, lam: float = 0.0, alpha: float = 1.0,
                  nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
                  sample_max: float = 1.0, check_every: int = 100, stream: int | None = None,
-                 step_balance: float = 1.0, adaptive_balance: bool = False):
+                 step_balance: float = 1.0, adaptive_balance: bool = False,
+                 anisotropic: bool = False):
         self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
         self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
-                              sample_min, sample_max, check_every, step_balance, adaptive_balance)
+                              sample_min, sample_max, check_every, step_balance, adaptive_balance,
+                              anisotropic)
         self._keep = (f, cost)
         self.h = lift_create(self.spec, stream)
         self._keep = None

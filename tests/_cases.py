@@ -34,7 +34,7 @@ def oracle_problem(c: dict) -> O.Problem:
                      f=None if c.get("f") is None else c["f"].astype(np.float64),
                      cost=None if c.get("cost") is None else c["cost"].astype(np.float64),
                      smin=c.get("sample_min", 0.0), smax=c.get("sample_max", 1.0),
-                     theta=c.get("theta", 1.0))
+                     theta=c.get("theta", 1.0), aniso=int(c.get("aniso", 0)))
 
 
 def crop(c: dict, y0: int, y1: int, x0: int, x1: int) -> dict:
@@ -60,7 +60,7 @@ def gpu_solver(c: dict, device_inputs: bool = True, **kw):
     return G.Solver(c["kind"], c["H"], c["W"], c["L"], c["gamma_min"], c["gamma_max"], c["lam"],
                     c.get("alpha", 1.0), c.get("nu", 0.0), f=f, cost=cost,
                     sample_min=c.get("sample_min", 0.0), sample_max=c.get("sample_max", 1.0),
-                    step_balance=c.get("theta", 1.0), **kw)
+                    step_balance=c.get("theta", 1.0), anisotropic=bool(c.get("aniso", 0)), **kw)
 
 
 def oracle_run(c: dict, iters: int):

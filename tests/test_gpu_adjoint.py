@@ -16,11 +16,11 @@ def _require_gpu():
         pytest.fail("CUDA device required for -m gpu tests")
 
 
-def _solver(kind, f, L, lam, alpha, nu, theta=1.0):
+def _solver(kind, f, L, lam, alpha, nu, theta=1.0, aniso=0):
     from paper_1512_01383_gb300 import lift as G
     H, W = f.shape
     return G.Solver(kind, H, W, L, 0.0, 1.0, lam, alpha, nu, f=torch.from_numpy(f).cuda(),
-                    step_balance=theta)
+                    step_balance=theta, anisotropic=bool(aniso))
 
 
 def _gpu_grads(s, iters, every, clean):
@@ -35,21 +35,22 @@ def _gpu_grads(s, iters, every, clean):
     return u.cpu().numpy(), gf.cpu().numpy(), np.array(sc)
 
 
-@pytest.mark.parametrize("kind,L,lam,alpha,nu,theta", [
-    (1, 5, 0.25, 25.0, 0.1, 1.0),
-    (0, 4, 0.2, 1.5, 0.0, 1.0),
-    (1, 9, 0.3, 20.0, 0.08, 1.0),
-    (1, 5, 0.25, 25.0, 0.1, 16.0),
+@pytest.mark.parametrize("kind,L,lam,alpha,nu,theta,aniso", [
+    (1, 5, 0.25, 25.0, 0.1, 1.0, 0),
+    (0, 4, 0.2, 1.5, 0.0, 1.0, 0),
+    (1, 9, 0.3, 20.0, 0.08, 1.0, 0),
+    (1, 5, 0.25, 25.0, 0.1, 16.0, 0),
+    (1, 5, 0.25, 25.0, 0.1, 1.0, 1),
 ])
-def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta):
+def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, aniso):
     _require_gpu()
     H, W, iters = 11, 9, 30
     noisy, clean = synth.voronoi_ramps(H, W, 81 + L, cells=4)
     f = synth.as_f32(noisy)
-    with _solver(kind, f, L, lam, alpha, nu, theta) as s:
+    with _solver(kind, f, L, lam, alpha, nu, theta, aniso) as s:
         u, gf, gs = _gpu_grads(s, iters, 7, clean)
     P = O.Problem(O.TRUNC if kind == 1 else O.QUAD, H, W, L, 0.0, 1.0, lam=lam, alpha=alpha,
-                  nu=nu, f=f.astype(np.float64), theta=theta)
+                  nu=nu, f=f.astype(np.float64), theta=theta, aniso=aniso)
     X = O.State(P)
     O.pdhg(P, X, iters)
     uo = O.unlift(P, X.u)

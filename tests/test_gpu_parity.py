@@ -335,3 +335,22 @@ def test_adaptive_balance_matches_oracle(L):
         ut = s.unlift()
     assert abs(th_g - th_o) <= 1e-3 * th_o, (th_g, th_o)
     assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() <= U_TOL
+
+
+@pytest.mark.parametrize("kind,H,W,L,iters", [(1, 29, 23, 5, 250), (0, 25, 21, 2, 250), (2, 17, 15, 6, 100)])
+def test_anisotropic_tv_matches_oracle(kind, H, W, L, iters):
+    """phi = |.|_1: box projection of p_i and l1 norms in the energies."""
+    _require_gpu()
+    c = case(kind, H, W, L, 1700 + L, aniso=1)
+    P, X = oracle_run(c, iters)
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        st = s.state()
+        Pg, Dg, Eg = s.energy()
+    rng = c["gamma_max"] - c["gamma_min"]
+    assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() / rng <= U_TOL
+    _compare_state(st, X, P, 2e-3)
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)

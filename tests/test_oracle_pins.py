@@ -532,3 +532,46 @@ def test_movement_is_weighted_squared_change():
     dx, dy = O.movement(P, Y, X)
     assert dx == pytest.approx(0.25 / st["tau_u"])
     assert dy == pytest.approx(4.0 / st["sigma_q"])
+
+
+# --------------------------------------------------------------------------
+# Anisotropic TV (Sec. 5.3: Props. 4-5 hold for phi = |.|_1)
+# --------------------------------------------------------------------------
+def test_anisotropic_L2_equals_direct_anisotropic_rof():
+    """With phi = |.|_1 and L = 2 the relaxation is box-constrained ROF with
+    the anisotropic TV |grad u|_1, solved independently."""
+    f = synth.gaussian_blobs(10, 9, 141)
+    P = O.Problem(O.QUAD, 10, 9, 2, 0.0, 1.0, lam=0.2, alpha=1.0, f=f, aniso=1)
+    X = O.State(P)
+    O.pdhg(P, X, 5000)
+    u_dir, gap = O.rof_direct(f, 1.0, 0.2, 0.0, 1.0, 100000, aniso=True)
+    assert gap < 1e-8
+    Er = O.rof_energy(u_dir, f, 1.0, 0.2, aniso=True)
+    Ph, D, E = O.energy(P, X)
+    assert D <= Er + 1e-12 and abs(Ph - Er) < 1e-7 * Er and abs(D - Er) < 1e-7 * Er
+    assert np.abs(O.unlift(P, X.u).reshape(10, 9) - u_dir).max() < 1e-4
+    # and the isotropic optimum differs (the two TVs are different energies)
+    Eiso = O.rof_energy(O.rof_direct(f, 1.0, 0.2, 0.0, 1.0, 20000)[0], f, 1.0, 0.2)
+    assert abs(Eiso - Er) > 1e-3 * Er
+
+
+def test_anisotropic_p_satisfies_infinite_constraints():
+    """Prop. 4 with phi = |.|_1: |q^T (1_i^a - 1_j^b)|_inf <= lambda |gamma_i^a - gamma_j^b|
+    on sampled (i, j, a, b) for the box-projected p."""
+    f = synth.voronoi_ramps(5, 6, 143)[0]
+    P = O.Problem(O.TRUNC, 5, 6, 6, 0.0, 1.0, lam=0.3, alpha=25.0, nu=0.1, f=f, aniso=1)
+    X = O.State(P)
+    O.pdhg(P, X, 40)
+    lab = O.labels(P.L, 0, 1)
+    p = np.stack([X.px, X.py], axis=-1)
+    assert np.abs(p).max() > 0
+    # box-projected: the l2 norm of some p_i exceeds the ball radius
+    assert (np.linalg.norm(p, axis=-1) > P.lam * np.diff(lab)[None, :] * (1 + 1e-9)).any()
+    r = synth.Rng(144)
+    for pix in range(P.N):
+        for _ in range(40):
+            j, i = sorted(r.integers(2, 0, P.k - 1))
+            a, b = r.uniform(2)
+            vec = p[pix, j:i].sum(0) + a * p[pix, i] - b * p[pix, j]
+            rhs = abs((lab[i] + a * (lab[i + 1] - lab[i])) - (lab[j] + b * (lab[j + 1] - lab[j])))
+            assert np.abs(vec).max() <= P.lam * rhs + 1e-12
