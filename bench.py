@@ -263,6 +263,28 @@ def run_stereo(G, torch, stream, dev):
     return out
 
 
+def run_phase(G, torch, stream, dev):
+    """Phase unwrapping (periodic quadratic pieces), 512x512 synthetic wrapped
+    phase, labels on [0, 4 pi], L=8, lambda=0.2, alpha=1: throughput of 200
+    iterations, then 5000 iterations from zero with the relative gap and the
+    mean |u~ - true phase| of the result (with a weaker lambda the relaxation
+    is not tight and the unlifted phase keeps 2 pi jumps)."""
+    from paper_1512_01383_gb300 import synth
+    w, true = synth.wrapped_phase(512, 512, synth.BASE_SEED + 5)
+    fd = torch.from_numpy(synth.as_f32(w)).to(dev)
+    L, n = 8, 5000
+    with G.Solver(G.LIFT_PERIODIC_QUAD, 512, 512, L, 0.0, float(4 * np.pi), 0.2, 1.0,
+                  float(2 * np.pi), f=fd, stream=stream.cuda_stream) as s:
+        ms = time_iters(G, torch, s, 200, stream)
+        s.reset()
+        s.iterate(n)
+        gap = s.gap()
+        err = float(np.abs(s.unlift().astype(np.float64) - true).mean())
+    return {"value": 512 * 512 * (L - 1) * 200 / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_iter": ms / 200, f"rel_gap_after_{n}_iters": gap,
+            f"mean_abs_error_vs_true_phase_after_{n}_iters": err}
+
+
 def run_differentiable(G, torch, stream, dev, iters=500, every=50):
     """Unrolled solve for differentiation: 256x256 truncated quadratic, L=16,
     500 iterations, checkpoints every 50; forward (checkpointed) and the
@@ -451,6 +473,7 @@ def main():
         extra["rof_64x64_L2"] = run_rof64(G, torch, stream, dev)
         extra["stereo_640x480"] = run_stereo(G, torch, stream, dev)
         extra["differentiable_256_L16"] = run_differentiable(G, torch, stream, dev)
+        extra["phase_unwrapping_512_L8"] = run_phase(G, torch, stream, dev)
 
     batch = None
     if not args.no_batch and rank == 0:

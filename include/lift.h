@@ -56,6 +56,13 @@ extern "C" {
  *  LIFT_PL_SAMPLED rho = piecewise-linear interpolant of n_samples costs
  *                  at positions sample_min + j (sample_max-sample_min)/
  *                  (n_samples-1)                        (Sec. 5.4 stereo)
+ *  LIFT_PERIODIC_QUAD  phase unwrapping (Sec. 5.5): the squared circular
+ *                  distance to the wrapped data f(x), approximated on each
+ *                  Gamma_i by the parabola alpha/2 (t - c_i)^2 of the
+ *                  periodic copy c_i = f + nu m (m integer, nu = the period,
+ *                  e.g. 2 pi) nearest to the interval's midpoint; at a
+ *                  label (within 1e-4 of an interval width) rho is the
+ *                  smaller of the two adjacent pieces
  * Each interval Gamma_i = [gamma_i, gamma_{i+1}] sees only the convex
  * envelope rho_i^** of rho restricted to it (Prop. 1).  For the two
  * quadratic kinds the envelope is linear-quadratic-linear and is derived in
@@ -65,15 +72,18 @@ extern "C" {
 #define LIFT_QUAD        0
 #define LIFT_TRUNC_QUAD  1
 #define LIFT_PL_SAMPLED  2
+#define LIFT_PERIODIC_QUAD 3
 
 typedef struct lift_spec {
-    int kind;                 /* LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED  */
+    int kind;                 /* LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED,
+                                 LIFT_PERIODIC_QUAD                         */
     int H, W;                 /* image size, H*W >= 1                        */
     int L;                    /* labels, 2 <= L <= LIFT_MAX_K + 1            */
     double gamma_min;         /* equidistant labels gamma_1 < ... < gamma_L  */
     double gamma_max;         /*   on [gamma_min, gamma_max] (Sec. 3)         */
     double lambda;            /* TV weight >= 0: ball radius lambda*Delta_i  */
-    double alpha, nu;         /* QUAD: alpha > 0.  TRUNC: alpha > 0, nu > 0  */
+    double alpha, nu;         /* QUAD: alpha > 0.  TRUNC: alpha > 0, nu > 0.
+                                 PERIODIC: alpha > 0, nu = period > 0      */
     const float *f;           /* QUAD/TRUNC: H*W row-major image             */
     const float *cost;        /* PL: H*W*n_samples, pixel-major              */
     int n_samples;            /* PL: >= 2                                    */

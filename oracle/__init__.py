@@ -6,7 +6,7 @@ no code with the CUDA path.  See ``lift_oracle.c`` for what each function
 computes and which passage of arXiv 1512.01383 it follows.
 """
 from .oracle import (  # noqa: F401
-    QUAD, TRUNC, PL, Problem, State, build, conj, lifted_conj, proj_epi, biconj,
+    QUAD, TRUNC, PL, PERIODIC, Problem, State, build, conj, lifted_conj, proj_epi, biconj,
     rho, grad, div, steps, pdhg, unlift, monotone_proj, energy, rof_direct,
     rof_energy, labels, unrolled_grad, movement, pdhg_adaptive,
 )

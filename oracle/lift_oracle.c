@@ -44,12 +44,15 @@
 /* ------------------------------------------------------------------------ */
 /* Problem description (owned by the caller, read-only here).               */
 /* ------------------------------------------------------------------------ */
-enum { ORC_QUAD = 0, ORC_TRUNC = 1, ORC_PL = 2 };
+enum { ORC_QUAD = 0, ORC_TRUNC = 1, ORC_PL = 2, ORC_PERIODIC = 3 };
 
 typedef struct {
     int kind;              /* ORC_QUAD: rho = alpha/2 (t-f)^2
                               ORC_TRUNC: rho = min(alpha (t-f)^2, nu)
-                              ORC_PL: rho = PL interpolant of sampled costs */
+                              ORC_PL: rho = PL interpolant of sampled costs
+                              ORC_PERIODIC: on Gamma_i, alpha/2 (t-c_i)^2,
+                              c_i the copy f + nu*m nearest the interval's
+                              midpoint (nu = period; Sec. 5.5) */
     int H, W, L;           /* image size, number of labels (k = L-1)      */
     double gmin, gmax;     /* label range Gamma = [gmin, gmax], equidistant */
     double lam;            /* TV weight lambda                             */
@@ -112,8 +115,46 @@ static double pl_pos(const orc_problem *P, int j)
     return P->smin + (P->smax - P->smin) * (double)j / (double)(P->ns - 1);
 }
 
+/* Phase unwrapping (Sec. 5.5): the squared circular distance d(t, f)^2 is
+   approximated on each interval Gamma_i by the parabola of the periodic copy
+   of f nearest to the interval's midpoint. */
+static double periodic_center(const orc_problem *P, int pix, int i)
+{
+    double mid = 0.5 * (gam(P, i) + gam(P, i + 1)), f = P->f[pix], per = P->nu;
+    return f + per * floor((mid - f) / per + 0.5);
+}
+
+static double periodic_piece(const orc_problem *P, int pix, int i, double t)
+{
+    double d = t - periodic_center(P, pix, i);
+    return 0.5 * P->alpha * d * d;
+}
+
+/* rho(t): the piece of the interval that contains t; at a label (within
+   1e-4 of an interval width, which covers single-precision rounding of a
+   value that sits on a label) the smaller of the two adjacent pieces. */
+static double periodic_rho(const orc_problem *P, int pix, double t)
+{
+    int k = P->L - 1;
+    double x = (t - P->gmin) / ((P->gmax - P->gmin) / (double)k);
+    int i0 = (int)floor(x);
+    if (i0 < 0) i0 = 0;
+    if (i0 > k - 1) i0 = k - 1;
+    double best = periodic_piece(P, pix, i0, t);
+    if (x - i0 < 1e-4 && i0 > 0) {
+        double b = periodic_piece(P, pix, i0 - 1, t);
+        if (b < best) best = b;
+    }
+    if ((double)(i0 + 1) - x < 1e-4 && i0 + 1 < k) {
+        double b = periodic_piece(P, pix, i0 + 1, t);
+        if (b < best) best = b;
+    }
+    return best;
+}
+
 double orc_rho(const orc_problem *P, int pix, double t)
 {
+    if (P->kind == ORC_PERIODIC) return periodic_rho(P, pix, t);
     if (P->kind == ORC_QUAD) {
         double d = t - P->f[pix];
         return 0.5 * P->alpha * d * d;
@@ -146,6 +187,12 @@ double orc_conj(const orc_problem *P, int pix, int i, double y, double *tmax)
         /* concave quadratic in t: stationary point f + y/alpha, clamped */
         double t = clampd(P->f[pix] + y / P->alpha, l, r);
         best = t * y - orc_rho(P, pix, t);
+        bt = t;
+    } else if (P->kind == ORC_PERIODIC) {
+        /* the interval's own parabola, centred at c_i */
+        double c = periodic_center(P, pix, i);
+        double t = clampd(c + y / P->alpha, l, r);
+        best = t * y - periodic_piece(P, pix, i, t);
         bt = t;
     } else if (P->kind == ORC_TRUNC) {
         /* -min(A,B) = max(-A,-B): the sup of the max is the max of the sups */
@@ -234,6 +281,10 @@ static double slope_bound(const orc_problem *P, int pix, int i)
     if (P->kind == ORC_QUAD) {
         double f = P->f[pix];
         return 1.0 + P->alpha * (fabs(l - f) + fabs(r - f));
+    }
+    if (P->kind == ORC_PERIODIC) {
+        double c = periodic_center(P, pix, i);
+        return 1.0 + P->alpha * (fabs(l - c) + fabs(r - c));
     }
     if (P->kind == ORC_TRUNC) {
         double f = P->f[pix];

@@ -14,7 +14,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-QUAD, TRUNC, PL = 0, 1, 2
+QUAD, TRUNC, PL, PERIODIC = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lift_oracle.c")

@@ -188,7 +188,9 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
         const D5 f = D5::seed(__ldg(P.f + pix), 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
         const float l = ic.x, r = ic.x + P.delta;
         QPieceT<D5> qp;
-        if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
+        if (P.kind == 3)
+            qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
+        else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
         else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
         D5 yo, ho;
         qpiece_project(qp, y0, h0, yo, ho);

@@ -96,7 +96,7 @@ bool is_finite(double x) { return std::isfinite(x); }
 
 int validate(const lift_spec *s)
 {
-    if (s->kind < LIFT_QUAD || s->kind > LIFT_PL_SAMPLED) return LIFT_ERR_SPEC;
+    if (s->kind < LIFT_QUAD || s->kind > LIFT_PERIODIC_QUAD) return LIFT_ERR_SPEC;
     if (s->H < 1 || s->W < 1) return LIFT_ERR_SPEC;
     if (s->L < 2 || s->L > LIFT_MAX_K + 1) return LIFT_ERR_SPEC;
     const long long N = static_cast<long long>(s->H) * s->W;
@@ -106,10 +106,10 @@ int validate(const lift_spec *s)
     if (!is_finite(s->lambda) || s->lambda < 0.0) return LIFT_ERR_SPEC;
     if (!is_finite(s->step_balance)) return LIFT_ERR_SPEC;
     if (s->tv_anisotropic != 0 && s->tv_anisotropic != 1) return LIFT_ERR_SPEC;
-    if (s->kind == LIFT_QUAD || s->kind == LIFT_TRUNC_QUAD) {
+    if (s->kind != LIFT_PL_SAMPLED) {
         if (!s->f) return LIFT_ERR_SPEC;
         if (!is_finite(s->alpha) || !(s->alpha > 0.0)) return LIFT_ERR_SPEC;
-        if (s->kind == LIFT_TRUNC_QUAD && (!is_finite(s->nu) || !(s->nu > 0.0))) return LIFT_ERR_SPEC;
+        if (s->kind != LIFT_QUAD && (!is_finite(s->nu) || !(s->nu > 0.0))) return LIFT_ERR_SPEC;
     } else {
         if (!s->cost || s->n_samples < 2) return LIFT_ERR_SPEC;
         if (!is_finite(s->sample_min) || !is_finite(s->sample_max) || !(s->sample_max > s->sample_min))
@@ -1052,7 +1052,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
     if (!is_finite(lambda) || lambda < 0.0) return LIFT_ERR_SPEC;
     if (h->kind != LIFT_PL_SAMPLED) {
         if (!is_finite(alpha) || !(alpha > 0.0)) return LIFT_ERR_SPEC;
-        if (h->kind == LIFT_TRUNC_QUAD && (!is_finite(nu) || !(nu > 0.0))) return LIFT_ERR_SPEC;
+        if (h->kind != LIFT_QUAD && (!is_finite(nu) || !(nu > 0.0))) return LIFT_ERR_SPEC;
     }
     std::vector<float4> ic(h->k);
     LIFT_CK(cudaMemcpyAsync(ic.data(), h->icst, h->k * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));

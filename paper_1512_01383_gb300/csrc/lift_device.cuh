@@ -246,9 +246,17 @@ __device__ __forceinline__ void pl_project(const float *__restrict__ t,
 // ---------------------------------------------------------------------------
 // Uniform access for the kernels.
 // ---------------------------------------------------------------------------
+// Phase unwrapping (kind 3): on [l, r] the parabola of the periodic copy
+// f + nu*m of the data nearest to the interval's midpoint (nu = period).
+__device__ __forceinline__ float periodic_center(float f, float per, float l, float r)
+{
+    return f + per * floorf((0.5f * (l + r) - f) / per + 0.5f);
+}
+
 __device__ __forceinline__ QPiece make_qpiece(const LiftParams &P, int pix, float l, float r)
 {
     const float f = __ldg(P.f + pix);
+    if (P.kind == 3) return make_quad_piece<float>(P.alpha, periodic_center(f, P.nu, l, r), l, r);
     return P.kind == 0 ? make_quad_piece<float>(P.alpha, f, l, r)
                        : make_trunc_piece<float>(P.alpha, P.nu, P.wtrunc, f, l, r);
 }
@@ -279,8 +287,9 @@ __device__ __forceinline__ float quad_conj_direct(const LiftParams &P, float f, 
         const float d = t - f;
         return fmaxf(t * y - P.alpha * d * d, fmaxf(l * y, r * y) - P.nu);
     }
-    const float t = fminf(fmaxf(f + y * P.inv_alpha, l), r);
-    const float d = t - f;
+    const float c = P.kind == 3 ? periodic_center(f, P.nu, l, r) : f;
+    const float t = fminf(fmaxf(c + y * P.inv_alpha, l), r);
+    const float d = t - c;
     return t * y - 0.5f * P.alpha * d * d;
 }
 
@@ -324,6 +333,23 @@ __device__ __forceinline__ float data_rho(const LiftParams &P, int pix, float t)
         const float a = x - (float)j;
         const float *c = P.cost + (size_t)pix * P.ns;
         return (1.0f - a) * __ldg(c + j) + a * __ldg(c + j + 1);
+    }
+    if (P.kind == 3) {
+        // the piece of the interval holding t; within 1e-4 of an interval width of
+        // a label (single-precision rounding of a value on it) the smaller of the two
+        const float x = (t - P.gmin) * P.inv_delta;
+        int i0 = static_cast<int>(floorf(x));
+        i0 = i0 < 0 ? 0 : (i0 > P.k - 1 ? P.k - 1 : i0);
+        const float f = __ldg(P.f + pix);
+        auto piece = [&](int i) {
+            const float l = P.gmin + P.delta * i;
+            const float d = t - periodic_center(f, P.nu, l, l + P.delta);
+            return 0.5f * P.alpha * d * d;
+        };
+        float best = piece(i0);
+        if (x - i0 < 1e-4f && i0 > 0) best = fminf(best, piece(i0 - 1));
+        if (static_cast<float>(i0 + 1) - x < 1e-4f && i0 + 1 < P.k) best = fminf(best, piece(i0 + 1));
+        return best;
     }
     const float d = t - __ldg(P.f + pix);
     if (P.kind == 0) return 0.5f * P.alpha * d * d;

@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED = 0, 1, 2
+LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED, LIFT_PERIODIC_QUAD = 0, 1, 2, 3
 LIFT_OK, LIFT_ERR_SPEC, LIFT_ERR_OOM, LIFT_ERR_CUDA = 0, 1, 2, 3
 LIFT_ERR_NAN, LIFT_ERR_NOT_CONVERGED, LIFT_ERR_ARG = 4, 5, 6
 LIFT_MAX_K = 64

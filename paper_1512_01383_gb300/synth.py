@@ -170,6 +170,26 @@ def stereo_cost(H: int, W: int, seed: int, ndisp: int = 65, tau: float = 0.2,
     return cost, disp
 
 
+def wrapped_phase(H: int, W: int, seed: int, lo: float = 1.0, hi: float = 11.0,
+                  noise: float = 0.1, period: float = 2.0 * np.pi) -> tuple[np.ndarray, np.ndarray]:
+    """Wrapped phase (stand-in for the SAR data of Sec. 5.5): a smooth
+    surface of 6 Gaussian bumps plus a seeded linear ramp, scaled to
+    [lo, hi], plus N(0, noise^2), wrapped into [0, period).
+    Returns (wrapped, true unwrapped)."""
+    r = Rng(seed, 6)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    gy, gx = r.uniform(2, -1, 1)
+    field = gx * xx / max(W, 1) + gy * yy / max(H, 1)
+    for _ in range(6):
+        cy, cx = r.uniform(1, 0, H)[0], r.uniform(1, 0, W)[0]
+        sg = r.uniform(1, 0.1, 0.3)[0] * max(H, W)
+        field = field + r.uniform(1, -1, 1)[0] * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * sg * sg))
+    a, b = field.min(), field.max()
+    true = lo + (hi - lo) * ((field - a) / (b - a) if b > a else np.zeros_like(field))
+    wrapped = np.mod(true + r.normal(H * W, noise).reshape(H, W), period)
+    return wrapped, true
+
+
 def batch_instances(n: int, seed: int, smin: int = 128, smax: int = 1024,
                     Ls=(4, 8, 16, 32)) -> list[tuple[int, int]]:
     """(side, L) for n serving-style instances: side ~ U{smin..smax}, L ~ U(Ls)."""

@@ -6,7 +6,7 @@ import numpy as np
 import oracle as O
 from paper_1512_01383_gb300 import synth
 
-KIND_ORACLE = {0: O.QUAD, 1: O.TRUNC, 2: O.PL}
+KIND_ORACLE = {0: O.QUAD, 1: O.TRUNC, 2: O.PL, 3: O.PERIODIC}
 
 
 def case(kind: int, H: int, W: int, L: int, seed: int, **kw) -> dict:
@@ -18,6 +18,10 @@ def case(kind: int, H: int, W: int, L: int, seed: int, **kw) -> dict:
         f = synth.as_f32(synth.voronoi_ramps(H, W, seed)[0])
         d = dict(kind=1, H=H, W=W, L=L, gamma_min=0.0, gamma_max=1.0, lam=0.25, alpha=25.0,
                  nu=0.1, f=f)
+    elif kind == 3:
+        f = synth.as_f32(synth.wrapped_phase(H, W, seed)[0])
+        d = dict(kind=3, H=H, W=W, L=L, gamma_min=0.0, gamma_max=float(4 * np.pi), lam=0.05,
+                 alpha=1.0, nu=float(2 * np.pi), f=f)
     else:
         ndisp = kw.pop("ndisp", 17)
         cost = synth.as_f32(synth.stereo_cost(H, W, seed, ndisp=ndisp)[0])

@@ -41,6 +41,7 @@ def _gpu_grads(s, iters, every, clean):
     (1, 9, 0.3, 20.0, 0.08, 1.0, 0),
     (1, 5, 0.25, 25.0, 0.1, 16.0, 0),
     (1, 5, 0.25, 25.0, 0.1, 1.0, 1),
+    (3, 6, 0.2, 1.5, 0.4, 1.0, 0),      # periodic pieces, period 0.4 on [0, 1]
 ])
 def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, aniso):
     _require_gpu()
@@ -49,7 +50,8 @@ def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, ani
     f = synth.as_f32(noisy)
     with _solver(kind, f, L, lam, alpha, nu, theta, aniso) as s:
         u, gf, gs = _gpu_grads(s, iters, 7, clean)
-    P = O.Problem(O.TRUNC if kind == 1 else O.QUAD, H, W, L, 0.0, 1.0, lam=lam, alpha=alpha,
+    okind = {0: O.QUAD, 1: O.TRUNC, 3: O.PERIODIC}[kind]
+    P = O.Problem(okind, H, W, L, 0.0, 1.0, lam=lam, alpha=alpha,
                   nu=nu, f=f.astype(np.float64), theta=theta, aniso=aniso)
     X = O.State(P)
     O.pdhg(P, X, iters)

@@ -575,3 +575,78 @@ def test_anisotropic_p_satisfies_infinite_constraints():
             vec = p[pix, j:i].sum(0) + a * p[pix, i] - b * p[pix, j]
             rhs = abs((lab[i] + a * (lab[i + 1] - lab[i])) - (lab[j] + b * (lab[j + 1] - lab[j])))
             assert np.abs(vec).max() <= P.lam * rhs + 1e-12
+
+
+# --------------------------------------------------------------------------
+# Phase unwrapping (Sec. 5.5): quadratic pieces of the periodic data
+# --------------------------------------------------------------------------
+def _periodic_piece(f, per, alpha, l, r, t):
+    c = f + per * np.floor((0.5 * (l + r) - f) / per + 0.5)
+    return 0.5 * alpha * (t - c) ** 2
+
+
+def test_periodic_pieces_conjugate_and_envelope():
+    """Each interval sees the parabola of the periodic copy of f nearest to
+    its midpoint: conjugate by brute force, envelope = the parabola itself."""
+    w, _ = synth.wrapped_phase(2, 3, 151)
+    per = 2 * np.pi
+    P = O.Problem(O.PERIODIC, 2, 3, 8, 0.0, 4 * np.pi, lam=0.005, alpha=1.0, nu=per, f=w)
+    lab = O.labels(8, 0.0, 4 * np.pi)
+    r = synth.Rng(152)
+    for pix in range(P.N):
+        for i in range(P.k):
+            grid = np.linspace(lab[i], lab[i + 1], 200001)
+            vals = _periodic_piece(P.f[pix], per, 1.0, lab[i], lab[i + 1], grid)
+            for y in r.uniform(5, -15, 15):
+                val, _ = O.conj(P, pix, i, y)
+                bf = np.max(grid * y - vals)
+                assert bf - 1e-12 <= val <= bf + 1e-7 * (1 + abs(bf))
+            for t in np.linspace(lab[i], lab[i + 1], 7):
+                want = _periodic_piece(P.f[pix], per, 1.0, lab[i], lab[i + 1], t)
+                assert abs(O.biconj(P, pix, i, t) - want) <= 1e-9 * (1 + want)
+    # at an interior point rho is the interval's piece; the pieces match the
+    # squared circular distance where the nearest copy does not change
+    t = 0.5 * (lab[2] + lab[3])
+    d = np.abs(((t - P.f[0]) + np.pi) % per - np.pi)
+    assert O.rho(P, 0, t) == pytest.approx(0.5 * d * d)
+
+
+def test_phase_unwrapping_recovers_the_ramp():
+    """A wrapped 1-D phase ramp from 1 to 11 rad (wraps twice) is unwrapped by
+    the relaxation with 8 labels on [0, 4 pi]: errors far below pi."""
+    w, true = synth.wrapped_phase(1, 48, 5)
+    P = O.Problem(O.PERIODIC, 1, 48, 8, 0.0, 4 * np.pi, lam=0.05, alpha=1.0, nu=2 * np.pi, f=w)
+    X = O.State(P)
+    O.pdhg(P, X, 4000)
+    err = np.abs(O.unlift(P, X.u) - true.ravel())
+    assert err.mean() < 0.15 and err.max() < 0.5, (err.mean(), err.max())
+    # wrapping only would leave errors of about 2 pi
+    assert np.abs(w.ravel() - true.ravel()).max() > 5.0
+
+
+def test_periodic_lambda0_circular_distance():
+    """lambda = 0 with labels on [1, 3] (less than one period): the optimum is
+    the per-pixel alpha/2 * (circular distance of f to [1, 3])^2, the textbook
+    distance over the copies f + 2 pi m, attained at the point of [1, 3]
+    nearest to the nearest copy."""
+    per, alpha = 2 * np.pi, 3.0
+    w, _ = synth.wrapped_phase(4, 5, 157)
+    P = O.Problem(O.PERIODIC, 4, 5, 5, 1.0, 3.0, lam=0.0, alpha=alpha, nu=per, f=w)
+    X = O.State(P)
+    copies = w.reshape(-1)[:, None] + per * np.array([-1.0, 0.0, 1.0])[None, :]
+    near = np.clip(copies, 1.0, 3.0)
+    dist = np.abs(copies - near)
+    m = np.argmin(dist, axis=1)
+    d = dist[np.arange(P.N), m]
+    tc = near[np.arange(P.N), m]
+    opt = 0.5 * alpha * float((d * d).sum())
+    assert opt > 1.0          # most pixels lie outside [1, 3]
+    gaps, errs = [], []
+    for _ in range(8):
+        O.pdhg(P, X, 2000)
+        Ph, D, E = O.energy(P, X)
+        assert D <= opt + 1e-9 and Ph >= opt - 1e-9
+        gaps.append(Ph - D)
+        errs.append(np.abs(O.unlift(P, X.u) - tc).max())
+    assert gaps[-1] < 0.1 * gaps[0] and gaps[-1] < 2e-3 * max(opt, 1.0)
+    assert errs[-1] < 1e-2, errs
