@@ -240,12 +240,16 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f,
 
 /* --------------------------------------------------------------- batches */
 /* A batch solves many independent problems (each its own size, label count
- * and data; one data-term kind, LIFT_QUAD or LIFT_TRUNC_QUAD) together: each
- * half-step is one launch over the tiles of every instance, and each
- * check_every iterations (of specs[0]) are replayed as one CUDA graph.
- * Instances found converged by lift_batch_solve stop iterating (their blocks
- * exit at once) while the others continue.  The iteration of each instance is
- * the same map as a single handle's (the same kernels on the same tiles). */
+ * and data; one quadratic data-term kind: LIFT_QUAD, LIFT_TRUNC_QUAD or
+ * LIFT_PERIODIC_QUAD) together.  Instances too small to fill the GPU share
+ * one launch per half-step over all their tiles; an instance with at least
+ * big_tiles tiles of 256 threads (two full waves of the GPU by default; see
+ * lift_batch_autotune) runs on the single-instance kernels instead, which
+ * reach full bandwidth on it alone.  Each check_every iterations (of
+ * specs[0]) are replayed as one CUDA graph.  Instances found converged by
+ * lift_batch_solve stop iterating (their blocks exit at once, through a
+ * device flag) while the others continue.  The iteration of each instance is
+ * the same map as a single handle's (the same per-tile arithmetic). */
 typedef struct lift_batch_ctx *lift_batch;
 
 /* lift_create_batch: n >= 1 specs (each validated as by lift_create; PL and
@@ -285,10 +289,26 @@ int lift_batch_unlift(lift_batch b, int i, float *out, int on_host);
 /* lift_batch_get_state: state image of instance i (layout of lift_get_state). */
 int lift_batch_get_state(lift_batch b, int i, void *dst, size_t bytes, int on_host);
 
-/* lift_batch_autotune: time `iters` iterations for tile widths of 128, 256
- * and 512 threads on this batch and keep the fastest (*threads_chosen, may
- * be NULL).  Resets every iterate to zero. */
+/* lift_batch_autotune: time `iters` iterations for each tile width of the
+ * merged launch (128, 256, 512 threads) and each big-instance threshold (none,
+ * 1, 2 or 4 full waves of 256-thread tiles) on this batch and keep the
+ * fastest (*threads_chosen, may be NULL).  Resets every iterate to zero. */
 int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen);
+
+/* lift_batch_set_schedule: set the schedule by hand: tile width of the
+ * merged launch (128, 256 or 512 threads, at least k of every instance left
+ * in it, else LIFT_ERR_ARG and the schedule is unchanged) and the
+ * big-instance threshold in 256-thread tiles (0: every instance merged; 1:
+ * every instance on the single-instance kernels).  The iterates are kept.
+ * With 256-thread tiles every instance follows its single handle's map
+ * bitwise; other widths change only the association order of the per-pixel
+ * sums over intervals. */
+int lift_batch_set_schedule(lift_batch b, int threads, int big_tiles);
+
+/* lift_batch_schedule: the current schedule: tile width of the merged
+ * launch, big-instance threshold in 256-thread tiles (0: none), and how many
+ * instances run on the single-instance kernels.  Any pointer may be NULL. */
+int lift_batch_schedule(lift_batch b, int *threads, int *big_tiles, int *n_big);
 
 /* ------------------------------------------------ allocation-free variant */
 /* lift_energy_noalloc: the energies of lift_energy for a state that the

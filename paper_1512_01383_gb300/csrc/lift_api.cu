@@ -635,15 +635,22 @@ const char *lift_strerror(int code)
 }  // extern "C"
 
 // ===========================================================================
-// Batches: many problem instances solved together (one launch per half-step
-// over all instances' tiles, captured in a CUDA graph per check interval).
+// Batches: many problem instances solved together.  Instances too small to
+// fill the GPU share one launch per half-step over all their tiles; an
+// instance with at least `big_tiles` 256-thread tiles fills it alone and runs
+// on the single-instance kernels (skipped through its live flag once
+// converged).  Every check interval is captured in one CUDA graph.
 // ===========================================================================
 struct lift_batch_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int n = 0, kind = 0, check_every = 100, threads = lift::kStepThreads;
+    int big_tiles = 0;                  // 0: every instance shares the merged launch
+    int wave = 1;                       // 256-thread tiles resident on the whole GPU
     std::vector<LiftParams> P;          // host copies (device pointers filled in)
     std::vector<LiftState> S;
+    std::vector<LiftParams> Pbig;       // single-kernel parameters of the big instances
+    std::vector<int> big;               // indices of the big instances
     std::vector<int> ntiles;            // per instance, for the current tile width
     void *arena = nullptr;              // all per-instance device arrays
     lift::InstDesc *desc = nullptr;     // device [n]
@@ -682,23 +689,40 @@ void free_batch(lift_batch b)
     delete b;
 }
 
-// (Re)build the tile list for a tile width of `threads` threads.
-int batch_set_tiles(lift_batch b, int threads)
+// (Re)build the tile list for a tile width of `threads` threads; instances
+// with at least big_tiles tiles of kStepThreads threads (big_tiles > 0) leave
+// the merged launch for the single-instance kernels.
+int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 {
     std::vector<lift::InstDesc> d(b->n);
     std::vector<int> ti;
     int t0 = 0;
+    b->big.clear();
+    b->Pbig.clear();
     for (int j = 0; j < b->n; ++j) {
+        LiftParams Ps = b->P[j];
+        Ps.ppb = lift::kStepThreads / Ps.k;
+        Ps.live = b->live + j;
+        const int nt_single = (Ps.N + Ps.ppb - 1) / Ps.ppb;
         b->P[j].ppb = threads / b->P[j].k;
         const int nt = (b->P[j].N + b->P[j].ppb - 1) / b->P[j].ppb;
-        b->ntiles[j] = nt;
         d[j].P = b->P[j];
         d[j].S = b->S[j];
+        if (big_tiles > 0 && nt_single >= big_tiles) {
+            b->big.push_back(j);
+            b->Pbig.push_back(Ps);
+            b->ntiles[j] = 0;
+            d[j].tile0 = 0;
+            d[j].ntiles = 0;
+            continue;
+        }
+        b->ntiles[j] = nt;
         d[j].tile0 = t0;
         d[j].ntiles = nt;
         ti.insert(ti.end(), nt, j);
         t0 += nt;
     }
+    if (ti.empty()) ti.push_back(0);    // keep a valid allocation; total_tiles stays 0
     if (b->tile_inst) cudaFree(b->tile_inst);
     b->tile_inst = nullptr;
     int rc = dev_alloc(reinterpret_cast<void **>(&b->tile_inst), ti.size() * sizeof(int));
@@ -710,15 +734,22 @@ int batch_set_tiles(lift_batch b, int threads)
     LIFT_CK(cudaStreamSynchronize(b->stream));   // host vectors die here
     b->total_tiles = t0;
     b->threads = threads;
+    b->big_tiles = big_tiles;
     drop_graph(b);
     return LIFT_OK;
 }
 
 int batch_launch(lift_batch b, int iters)
 {
-    for (int it = 0; it < iters; ++it)
+    for (int it = 0; it < iters; ++it) {
         LIFT_CK(lift::launch_batch_iteration(b->kind, b->threads, b->desc, b->tile_inst, b->live,
                                              b->total_tiles, b->stream));
+        for (size_t m = 0; m < b->big.size(); ++m) {
+            const LiftState &S = b->S[b->big[m]];
+            LIFT_CK(lift::launch_dual_step(b->Pbig[m], S, b->stream));
+            LIFT_CK(lift::launch_primal_step(b->Pbig[m], S, b->stream));
+        }
+    }
     return LIFT_OK;
 }
 
@@ -825,7 +856,13 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
             return LIFT_ERR_CUDA;
         }
     }
-    rc = batch_set_tiles(b, lift::kStepThreads);   // synchronises (ics die here)
+    {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        b->wave = std::max(1, sms * (2048 / lift::kStepThreads));
+    }
+    rc = batch_set_tiles(b, lift::kStepThreads, 2 * b->wave);   // synchronises (ics die here)
     if (rc == LIFT_OK) rc = lift_batch_reset(b);
     if (rc != LIFT_OK) { free_batch(b); return rc; }
     *out = b;
@@ -965,35 +1002,67 @@ int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen)
 {
     if (!b || iters < 1) return LIFT_ERR_ARG;
     const int cand[3] = {128, 256, 512};
+    // big-instance thresholds: none (all merged), 1, 2 and 4 full waves of
+    // 256-thread tiles
+    const int thr[4] = {0, b->wave, 2 * b->wave, 4 * b->wave};
     float best_ms = 0.0f;
-    int best = lift::kStepThreads;
+    int best = lift::kStepThreads, best_big = b->big_tiles;
     cudaEvent_t e0, e1;
     LIFT_CK(cudaEventCreate(&e0));
     LIFT_CK(cudaEventCreate(&e1));
     int rc = LIFT_OK;
-    for (int c = 0; c < 3 && rc == LIFT_OK; ++c) {
-        bool ok = true;
-        for (int j = 0; j < b->n; ++j) ok = ok && cand[c] >= b->P[j].k;
-        if (!ok) continue;
-        rc = batch_set_tiles(b, cand[c]);
-        if (rc == LIFT_OK) rc = lift_batch_reset(b);
-        if (rc == LIFT_OK) rc = batch_launch(b, 2);           // warm-up
-        if (rc != LIFT_OK) break;
-        cudaEventRecord(e0, b->stream);
-        rc = batch_launch(b, iters);
-        cudaEventRecord(e1, b->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LIFT_ERR_CUDA; break; }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = cand[c]; }
+    for (int t = 0; t < 4 && rc == LIFT_OK; ++t) {
+        for (int c = 0; c < 3 && rc == LIFT_OK; ++c) {
+            rc = batch_set_tiles(b, cand[c], thr[t]);
+            if (rc != LIFT_OK) break;
+            // every instance left in the merged launch needs a tile of >= k threads
+            bool ok = true;
+            for (int j = 0; j < b->n; ++j) ok = ok && (b->ntiles[j] == 0 || cand[c] >= b->P[j].k);
+            if (!ok) continue;
+            rc = lift_batch_reset(b);
+            if (rc == LIFT_OK) rc = batch_launch(b, 2);           // warm-up
+            if (rc != LIFT_OK) break;
+            cudaEventRecord(e0, b->stream);
+            rc = batch_launch(b, iters);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LIFT_ERR_CUDA; break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = cand[c]; best_big = thr[t]; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LIFT_OK) return rc;
-    rc = batch_set_tiles(b, best);
+    rc = batch_set_tiles(b, best, best_big);
     if (rc == LIFT_OK) rc = lift_batch_reset(b);
     if (rc == LIFT_OK && threads_chosen) *threads_chosen = best;
     return rc;
+}
+
+int lift_batch_set_schedule(lift_batch b, int threads, int big_tiles)
+{
+    if (!b || big_tiles < 0 || (threads != 128 && threads != 256 && threads != 512))
+        return LIFT_ERR_ARG;
+    const int old_threads = b->threads, old_big = b->big_tiles;
+    int rc = batch_set_tiles(b, threads, big_tiles);
+    if (rc != LIFT_OK) return rc;
+    for (int j = 0; j < b->n; ++j)
+        if (b->ntiles[j] > 0 && threads < b->P[j].k) {
+            // a merged instance needs a tile of >= k threads: keep the old schedule
+            rc = batch_set_tiles(b, old_threads, old_big);
+            return rc != LIFT_OK ? rc : LIFT_ERR_ARG;
+        }
+    return LIFT_OK;
+}
+
+int lift_batch_schedule(lift_batch b, int *threads, int *big_tiles, int *n_big)
+{
+    if (!b) return LIFT_ERR_ARG;
+    if (threads) *threads = b->threads;
+    if (big_tiles) *big_tiles = b->big_tiles;
+    if (n_big) *n_big = static_cast<int>(b->big.size());
+    return LIFT_OK;
 }
 
 }  // extern "C"

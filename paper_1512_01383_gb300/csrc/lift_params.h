@@ -33,6 +33,8 @@ struct LiftParams {
     const int *bstart;       // [k+1] first breakpoint of each interval (PL)
     int nb, ns;              // breakpoints, samples (PL)
     float smin, sh;          // sample j sits at smin + j*sh (PL)
+    const int *live;         // batch member run by the single-instance kernels:
+                             // their blocks return while *live == 0 (null: run)
 };
 
 // Device state of one problem instance (all float32, see include/lift.h).

@@ -238,6 +238,7 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
 {
     __shared__ float s_in[kStepThreads];
     __shared__ float s_last[kStepThreads / 32];
+    if (P.live != nullptr && *P.live == 0) return;
     dual_tile<KIND, kStepThreads>(P, xbar, y, q, blockIdx.x, s_in, s_last);
 }
 
@@ -250,6 +251,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
 {
     __shared__ float2 s_in[kStepThreads];
     __shared__ float2 s_last[kStepThreads / 32];
+    if (P.live != nullptr && *P.live == 0) return;
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);

@@ -28,7 +28,8 @@ EXPORTED = (
     "lift_energy_noalloc",
     "lift_create_batch", "lift_batch_destroy", "lift_batch_size", "lift_batch_reset",
     "lift_batch_iterate", "lift_batch_solve", "lift_batch_energy", "lift_batch_unlift",
-    "lift_batch_get_state", "lift_batch_autotune",
+    "lift_batch_get_state", "lift_batch_autotune", "lift_batch_schedule",
+    "lift_batch_set_schedule",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
     "lift_get_balance",
 )
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH):
         "lift_batch_unlift": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "lift_batch_get_state": (C.c_int, [vp, C.c_int, vp, C.c_size_t, C.c_int]),
         "lift_batch_autotune": (C.c_int, [vp, C.c_int, ip]),
+        "lift_batch_schedule": (C.c_int, [vp, ip, ip, ip]),
+        "lift_batch_set_schedule": (C.c_int, [vp, C.c_int, C.c_int]),
         "lift_set_params": (C.c_int, [vp, C.c_double, C.c_double, C.c_double]),
         "lift_unrolled_forward": (C.c_int, [vp, C.c_int, C.c_int]),
         "lift_unrolled_backward": (C.c_int, [vp, vp, vp, dp]),
@@ -408,6 +411,20 @@ def lift_batch_autotune(b: int, iters: int) -> int:
     t = C.c_int()
     _check(load().lift_batch_autotune(C.c_void_p(b), iters, C.byref(t)), "lift_batch_autotune")
     return t.value
+
+
+def lift_batch_set_schedule(b: int, threads: int, big_tiles: int) -> None:
+    _check(load().lift_batch_set_schedule(C.c_void_p(b), threads, big_tiles),
+           "lift_batch_set_schedule")
+
+
+def lift_batch_schedule(b: int) -> tuple[int, int, int]:
+    """(merged tile width, big-instance threshold in 256-thread tiles, number
+    of instances on the single-instance kernels)."""
+    t, g, n = C.c_int(), C.c_int(), C.c_int()
+    _check(load().lift_batch_schedule(C.c_void_p(b), C.byref(t), C.byref(g), C.byref(n)),
+           "lift_batch_schedule")
+    return t.value, g.value, n.value
 
 
 # ---------------------------------------------------------------------------

@@ -94,3 +94,9 @@ def test_null_arguments(lib):
     assert L.lift_unlift(None, None, 0) == lib.LIFT_ERR_ARG
     assert L.lift_state_bytes(None) == 0
     L.lift_destroy(None)
+    assert L.lift_create_batch(None, 0, None, None) == lib.LIFT_ERR_ARG
+    assert L.lift_batch_iterate(None, 3) == lib.LIFT_ERR_ARG
+    assert L.lift_batch_set_schedule(None, 256, 0) == lib.LIFT_ERR_ARG
+    assert L.lift_batch_schedule(None, None, None, None) == lib.LIFT_ERR_ARG
+    assert L.lift_batch_size(None) == 0
+    L.lift_batch_destroy(None)

@@ -29,12 +29,21 @@ def _batch(cases, check_every=50):
     return b, keep
 
 
-def test_batch_equals_single_handles_bitwise():
+# big-instance thresholds in 256-thread tiles: 0 merges every instance, 1 runs
+# every instance on the single-instance kernels, 17 splits SHAPES 3 / 3
+# (their tile counts are 17, 40, 10, 11, 257, 1)
+SCHEDULES = [(0, 0), (1, len(SHAPES)), (17, 3)]
+
+
+@pytest.mark.parametrize("big_tiles,n_big", SCHEDULES)
+def test_batch_equals_single_handles_bitwise(big_tiles, n_big):
     _require_gpu()
     from paper_1512_01383_gb300 import lift as G
     cases = [case(1, H, W, L, 1200 + j) for j, (H, W, L) in enumerate(SHAPES)]
     b, keep = _batch(cases)
     try:
+        G.lift_batch_set_schedule(b, 256, big_tiles)
+        assert G.lift_batch_schedule(b) == (256, big_tiles, n_big)
         G.lift_batch_iterate(b, 130)          # two graph replays + 30 direct iterations
         e = G.lift_batch_energy(b)
         for j, c in enumerate(cases):
@@ -76,13 +85,15 @@ def test_batch_instance_matches_oracle():
         G.lift_batch_destroy(b)
 
 
-def test_batch_solve_stops_converged_instances():
+@pytest.mark.parametrize("big_tiles", [0, 1])
+def test_batch_solve_stops_converged_instances(big_tiles):
     _require_gpu()
     from paper_1512_01383_gb300 import lift as G
     cases = [case(1, H, W, L, 1400 + j, theta=float((L - 1) ** 2))
              for j, (H, W, L) in enumerate([(24, 24, 3), (40, 32, 5), (16, 48, 9)])]
     b, keep = _batch(cases, check_every=100)
     try:
+        G.lift_batch_set_schedule(b, 256, big_tiles)
         rc, iters, nconv = G.lift_batch_solve(b, 40000, 1e-4)
         assert rc == G.LIFT_OK and nconv == len(cases)
         assert all(i > 0 and i % 100 == 0 for i in iters)
@@ -114,7 +125,7 @@ def test_batch_autotune_keeps_results():
     b, keep = _batch(cases)
     try:
         t = G.lift_batch_autotune(b, 5)
-        assert t in (128, 256, 512)
+        assert t in (128, 256, 512) and G.lift_batch_schedule(b)[0] == t
         G.lift_batch_iterate(b, 80)
         for j, c in enumerate(cases):
             P, X = oracle_run(c, 80)
@@ -135,3 +146,21 @@ def test_batch_rejects_mixed_or_pl_kinds():
     with pytest.raises(G.LiftError) as e:
         G.lift_create_batch(specs)
     assert e.value.code == G.LIFT_ERR_SPEC
+
+
+def test_batch_schedule_rejects_invalid_arguments():
+    """A tile width other than 128/256/512 or a negative threshold is an
+    argument error and leaves the schedule as it was."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    cases = [case(1, 9, 11, 5, 1600), case(1, 10, 7, 3, 1601)]
+    b, keep = _batch(cases)
+    try:
+        before = G.lift_batch_schedule(b)
+        with pytest.raises(G.LiftError):
+            G.lift_batch_set_schedule(b, 200, 0)
+        with pytest.raises(G.LiftError):
+            G.lift_batch_set_schedule(b, 256, -1)
+        assert G.lift_batch_schedule(b) == before
+    finally:
+        G.lift_batch_destroy(b)

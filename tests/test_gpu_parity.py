@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 from _cases import case, crop, gpu_solver, oracle_problem, oracle_run
+from paper_1512_01383_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -376,3 +377,28 @@ def test_phase_unwrapping_matches_oracle(H, W, L, iters):
     # itself stays at 1e-5 on a shared state (test_energy_kernel_on_oracle_state)
     for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
         assert abs(g - o) <= 5 * E_TOL * max(abs(o), 1.0), (g, o)
+
+
+@pytest.mark.parametrize("L,iters", [(5, 200), (12, 150)])
+def test_baseline_lifting_matches_oracle(L, iters):
+    """The baseline lifting (Prop. 2): the PL kind with the cost sampled only
+    at the labels, so every interval holds no interior sample and rho_i** is
+    the chord.  Samples of the truncated quadratic of the denoising workload."""
+    _require_gpu()
+    H, W = 19, 26
+    f = synth.voronoi_ramps(H, W, 1900 + L)[0]
+    lab = O.labels(L, 0.0, 1.0)
+    cost = synth.as_f32(np.minimum(25.0 * (lab[None, None, :] - f[:, :, None]) ** 2, 0.1))
+    c = dict(kind=2, H=H, W=W, L=L, gamma_min=0.0, gamma_max=1.0, lam=0.25, cost=cost,
+             sample_min=0.0, sample_max=1.0)
+    P, X = oracle_run(c, iters)
+    with gpu_solver(c) as s:
+        s.iterate(iters)
+        ut = s.unlift()
+        st = s.state()
+        Pg, Dg, Eg = s.energy()
+    assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() <= U_TOL
+    _compare_state(st, X, P, 2e-3)
+    Po, Do, Eo = O.energy(P, X)
+    for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
