@@ -8,5 +8,6 @@ computes and which passage of arXiv 1512.01383 it follows.
 from .oracle import (  # noqa: F401
     QUAD, TRUNC, PL, PERIODIC, Problem, State, build, conj, lifted_conj, proj_epi, biconj,
     rho, grad, div, steps, pdhg, unlift, monotone_proj, energy, rof_direct,
-    rof_energy, labels, unrolled_grad, movement, pdhg_adaptive,
+    rof_energy, labels, unrolled_grad, movement, pdhg_adaptive, grad3, div3, rof_direct3,
+    rof_energy3,
 )

@@ -21,7 +21,8 @@
  *   - the PDHG iteration on the saddle-point problem of Sec. 4
  *     (eq. discrete_saddle_point_final with the set C of eq. constraint_C,
  *     the z-splitting of eq. equality_constr_data and its multiplier s,
- *     the l2-ball set K of Prop. 5, forward differences on a Cartesian grid),
+ *     the l2-ball set K of Prop. 5, forward differences on a Cartesian grid
+ *     of d = 2 (image) or d = 3 (volume) axes, p_i in R^d),
  *     with the diagonal preconditioning of Pock-Chambolle (alpha = 1).
  *
  * Readings of points the paper leaves open (each also listed in the design doc):
@@ -64,27 +65,38 @@ typedef struct {
     double theta;          /* primal/dual step balance (<= 0 means 1)      */
     int aniso;             /* 1: phi(nu) = |nu|_1 (anisotropic TV), K is a  */
                            /*    product of l-infinity boxes; 0: |nu|_2     */
+    int D;                 /* depth: D > 1 makes the domain a D x H x W     */
+                           /* volume (voxel (z*H + y)*W + x, three forward  */
+                           /* differences); D <= 1 is the 2-D image         */
 } orc_problem;
 
 /* The norm phi of the jump direction in Phi_{i,j} (eq. regularizer_single)
    and the projection onto the dual-norm ball of radius R (Prop. 5 holds for
-   any convex one-homogeneous phi, Sec. 5.3). */
-static double tv_norm(int aniso, double a, double b)
+   any convex one-homogeneous phi, Sec. 5.3).  Three components; a 2-D image
+   passes c = 0. */
+static double tv_norm(int aniso, double a, double b, double c)
 {
-    return aniso ? fabs(a) + fabs(b) : sqrt(a * a + b * b);
+    return aniso ? fabs(a) + fabs(b) + fabs(c) : sqrt(a * a + b * b + c * c);
 }
 
-static void tv_project(int aniso, double R, double *a, double *b)
+static double clamp_abs(double a, double R)
+{
+    return a > R ? R : (a < -R ? -R : a);
+}
+
+static void tv_project(int aniso, double R, double *a, double *b, double *c)
 {
     if (aniso) {
-        *a = *a > R ? R : (*a < -R ? -R : *a);
-        *b = *b > R ? R : (*b < -R ? -R : *b);
+        *a = clamp_abs(*a, R);
+        *b = clamp_abs(*b, R);
+        *c = clamp_abs(*c, R);
         return;
     }
-    double nrm = sqrt(*a * *a + *b * *b);
+    double nrm = sqrt(*a * *a + *b * *b + *c * *c);
     double sc = nrm > R ? (nrm > 0.0 ? R / nrm : 0.0) : 1.0;
     *a *= sc;
     *b *= sc;
+    *c *= sc;
 }
 
 /* PDHG state; all arrays caller-allocated, index [pixel*k + i]. */
@@ -94,7 +106,15 @@ typedef struct {
     double *v, *z;         /* dual: data-term dual and scaled epigraph var */
     double *px, *py;       /* dual: TV dual p_i in R^2                     */
     double *q;             /* dual: epigraph height, one per pixel         */
+    double *pz;            /* dual: third component of p_i (D > 1 only)    */
 } orc_state;
+
+static int depth(const orc_problem *P) { return P->D > 1 ? P->D : 1; }
+
+static size_t npix(const orc_problem *P)
+{
+    return (size_t)depth(P) * P->H * P->W;
+}
 
 static double gam(const orc_problem *P, int j)   /* gamma_{j+1}, j = 0..k */
 {
@@ -324,31 +344,53 @@ double orc_biconj(const orc_problem *P, int pix, int i, double t)
 /* Forward differences with Neumann boundary (Sec. 4) and div = -grad^T.     */
 /* Arrays are [pixel*k + i].                                                 */
 /* ------------------------------------------------------------------------ */
+/* A D x H x W volume (D = 1: an image); gz may be NULL when D = 1. */
+void orc_grad3(int D, int H, int W, int k, const double *u, double *gx, double *gy,
+               double *gz)
+{
+    size_t row = (size_t)W * k, slice = (size_t)H * W * k;
+    for (int zz = 0; zz < D; ++zz)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int i = 0; i < k; ++i) {
+                    size_t o = (((size_t)zz * H + y) * W + x) * k + i;
+                    gx[o] = x + 1 < W ? u[o + k] - u[o] : 0.0;
+                    gy[o] = y + 1 < H ? u[o + row] - u[o] : 0.0;
+                    if (gz) gz[o] = zz + 1 < D ? u[o + slice] - u[o] : 0.0;
+                }
+}
+
+void orc_div3(int D, int H, int W, int k, const double *px, const double *py,
+              const double *pz, double *d)
+{
+    size_t row = (size_t)W * k, slice = (size_t)H * W * k;
+    for (int zz = 0; zz < D; ++zz)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int i = 0; i < k; ++i) {
+                    size_t o = (((size_t)zz * H + y) * W + x) * k + i;
+                    double a = 0.0;
+                    if (x + 1 < W) a += px[o];
+                    if (x > 0) a -= px[o - k];
+                    if (y + 1 < H) a += py[o];
+                    if (y > 0) a -= py[o - row];
+                    if (pz) {
+                        if (zz + 1 < D) a += pz[o];
+                        if (zz > 0) a -= pz[o - slice];
+                    }
+                    d[o] = a;
+                }
+}
+
 void orc_grad(int H, int W, int k, const double *u, double *gx, double *gy)
 {
-    for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x)
-            for (int i = 0; i < k; ++i) {
-                size_t o = ((size_t)y * W + x) * k + i;
-                gx[o] = x + 1 < W ? u[o + k] - u[o] : 0.0;
-                gy[o] = y + 1 < H ? u[o + (size_t)W * k] - u[o] : 0.0;
-            }
+    orc_grad3(1, H, W, k, u, gx, gy, NULL);
 }
 
 void orc_div(int H, int W, int k, const double *px, const double *py,
              double *d)
 {
-    for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x)
-            for (int i = 0; i < k; ++i) {
-                size_t o = ((size_t)y * W + x) * k + i;
-                double a = 0.0;
-                if (x + 1 < W) a += px[o];
-                if (x > 0) a -= px[o - k];
-                if (y + 1 < H) a += py[o];
-                if (y > 0) a -= py[o - (size_t)W * k];
-                d[o] = a;
-            }
+    orc_div3(1, H, W, k, px, py, NULL, d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -357,8 +399,9 @@ void orc_div(int H, int W, int k, const double *px, const double *py,
 /*   v_l : u_l + sum_{j>l} Delta_j s_j - gamma_l s_l                         */
 /*   z_i : s_i          q : -sum_i Delta_i s_i        p_i : grad u_i         */
 /* The (v_i, z_i) pair is projected jointly, so it shares one step (the      */
-/* smaller of its two rows); both components of p_i share 1/2; the column   */
-/* of u uses the interior count 1 + 4.  A balance theta > 0 then multiplies  */
+/* smaller of its two rows); every component of p_i shares 1/2; the column  */
+/* of u uses the interior count 1 + 2 * (number of axes), 1 + 4 on an image */
+/* and 1 + 6 on a volume.  A balance theta > 0 then multiplies              */
 /* every primal step and divides every dual step: the products tau*sigma,    */
 /* and with them the convergence condition of the preconditioned method,    */
 /* are unchanged; theta is the primal/dual balance that the adaptive step    */
@@ -372,7 +415,7 @@ typedef struct {
 static void make_steps(const orc_problem *P, orc_steps *S)
 {
     int k = P->L - 1;
-    S->tau_u = 1.0 / 5.0;
+    S->tau_u = 1.0 / (1.0 + 2.0 * (depth(P) > 1 ? 3.0 : 2.0));
     S->sigma_q = 1.0 / (gam(P, k) - gam(P, 0));
     S->sigma_p = 0.5;
     S->tau_s = (double *)malloc(sizeof(double) * k);
@@ -421,18 +464,22 @@ void orc_steps_get(const orc_problem *P, double *tau_u, double *sigma_q,
 /* ------------------------------------------------------------------------ */
 int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
 {
-    int H = P->H, W = P->W, k = P->L - 1;
-    size_t N = (size_t)H * W, Nk = N * k;
+    int H = P->H, W = P->W, k = P->L - 1, Dz = depth(P);
+    size_t N = npix(P), Nk = N * k;
+    if (Dz > 1 && !X->pz) return -2;
     orc_steps S;
     make_steps(P, &S);
     double *gx = (double *)malloc(sizeof(double) * Nk);
     double *gy = (double *)malloc(sizeof(double) * Nk);
+    double *gz = (double *)malloc(sizeof(double) * Nk);
     double *dv = (double *)malloc(sizeof(double) * Nk);
-    if (!gx || !gy || !dv) { free(gx); free(gy); free(dv); free_steps(&S); return -1; }
+    if (!gx || !gy || !gz || !dv) {
+        free(gx); free(gy); free(gz); free(dv); free_steps(&S); return -1;
+    }
 
     for (int n = 0; n < iters; ++n) {
         /* ---- dual step ---- */
-        orc_grad(H, W, k, X->ubar, gx, gy);
+        orc_grad3(Dz, H, W, k, X->ubar, gx, gy, gz);
         for (size_t pix = 0; pix < N; ++pix) {
             double *v = X->v + pix * k, *z = X->z + pix * k;
             double *px = X->px + pix * k, *py = X->py + pix * k;
@@ -442,9 +489,11 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
                 double d = gam(P, i + 1) - gam(P, i);
                 double ax = px[i] + S.sigma_p * gx[pix * k + i];
                 double ay = py[i] + S.sigma_p * gy[pix * k + i];
-                tv_project(P->aniso, P->lam * d, &ax, &ay);
+                double az = Dz > 1 ? X->pz[pix * k + i] + S.sigma_p * gz[pix * k + i] : 0.0;
+                tv_project(P->aniso, P->lam * d, &ax, &ay, &az);
                 px[i] = ax;
                 py[i] = ay;
+                if (Dz > 1) X->pz[pix * k + i] = az;
             }
             /* data duals: ascent on v, z, q */
             double tot = 0.0;
@@ -466,7 +515,7 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
             }
         }
         /* ---- primal step ---- */
-        orc_div(H, W, k, X->px, X->py, dv);
+        orc_div3(Dz, H, W, k, X->px, X->py, Dz > 1 ? X->pz : NULL, dv);
         for (size_t pix = 0; pix < N; ++pix) {
             const double *v = X->v + pix * k, *z = X->z + pix * k;
             double *u = X->u + pix * k, *s = X->s + pix * k;
@@ -484,7 +533,7 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
             }
         }
     }
-    free(gx); free(gy); free(dv);
+    free(gx); free(gy); free(gz); free(dv);
     free_steps(&S);
     return 0;
 }
@@ -495,7 +544,7 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
 void orc_unlift(const orc_problem *P, const double *u, double *out)
 {
     int k = P->L - 1;
-    size_t N = (size_t)P->H * P->W;
+    size_t N = npix(P);
     for (size_t pix = 0; pix < N; ++pix) {
         double a = gam(P, 0);
         for (int i = 0; i < k; ++i)
@@ -547,17 +596,18 @@ void orc_monotone_proj(int k, const double *u, double *w)
 void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
                 double *Dual, double *Enc)
 {
-    int H = P->H, W = P->W, k = P->L - 1;
-    size_t N = (size_t)H * W, Nk = N * k;
+    int H = P->H, W = P->W, k = P->L - 1, Dz = depth(P);
+    size_t N = npix(P), Nk = N * k;
     double *dv = (double *)malloc(sizeof(double) * Nk);
     double *uf = (double *)malloc(sizeof(double) * Nk);
     double *gx = (double *)malloc(sizeof(double) * Nk);
     double *gy = (double *)malloc(sizeof(double) * Nk);
+    double *gz = (double *)malloc(sizeof(double) * Nk);
     double *ut = (double *)malloc(sizeof(double) * N);
     double *S = (double *)malloc(sizeof(double) * (k + 1));
 
     /* dual bound */
-    orc_div(H, W, k, X->px, X->py, dv);
+    orc_div3(Dz, H, W, k, X->px, X->py, Dz > 1 ? X->pz : NULL, dv);
     double D = 0.0;
     for (size_t pix = 0; pix < N; ++pix) {
         double a = 0.0;
@@ -590,29 +640,25 @@ void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
             Pd += li * orc_biconj(P, (int)pix, i, gam(P, i) + a * d);
         }
     }
-    orc_grad(H, W, k, uf, gx, gy);
+    orc_grad3(Dz, H, W, k, uf, gx, gy, gz);
     double tv = 0.0;
     for (size_t o = 0; o < Nk; ++o) {
         int i = (int)(o % k);
-        tv += (gam(P, i + 1) - gam(P, i)) * tv_norm(P->aniso, gx[o], gy[o]);
+        tv += (gam(P, i + 1) - gam(P, i)) * tv_norm(P->aniso, gx[o], gy[o], gz[o]);
     }
     Pd += P->lam * tv;
 
-    /* nonconvex energy of the unlifted image */
+    /* nonconvex energy of the unlifted image (volume) */
     orc_unlift(P, X->u, ut);
+    orc_grad3(Dz, H, W, 1, ut, gx, gy, gz);
     double E = 0.0;
-    for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x) {
-            size_t pix = (size_t)y * W + x;
-            double ax = x + 1 < W ? ut[pix + 1] - ut[pix] : 0.0;
-            double ay = y + 1 < H ? ut[pix + W] - ut[pix] : 0.0;
-            E += orc_rho(P, (int)pix, ut[pix]) + P->lam * tv_norm(P->aniso, ax, ay);
-        }
+    for (size_t pix = 0; pix < N; ++pix)
+        E += orc_rho(P, (int)pix, ut[pix]) + P->lam * tv_norm(P->aniso, gx[pix], gy[pix], gz[pix]);
 
     *Phat = Pd;
     *Dual = D;
     *Enc = E;
-    free(dv); free(uf); free(gx); free(gy); free(ut); free(S);
+    free(dv); free(uf); free(gx); free(gy); free(gz); free(ut); free(S);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -623,43 +669,49 @@ void orc_energy(const orc_problem *P, const orc_state *X, double *Phat,
 /* and the tightness of the relaxation for convex data terms.               */
 /* Returns the final primal-dual gap.                                        */
 /* ------------------------------------------------------------------------ */
-static int g_rof_aniso = 0;   /* set by orc_rof_direct_aniso for its duration */
-
-static double rof_primal(int H, int W, const double *u, const double *f,
-                         double alpha, double lam)
+static double rof_primal(int D, int H, int W, const double *u, const double *f,
+                         double alpha, double lam, int aniso)
 {
+    size_t N = (size_t)D * H * W;
+    double *gx = (double *)malloc(sizeof(double) * N);
+    double *gy = (double *)malloc(sizeof(double) * N);
+    double *gz = (double *)malloc(sizeof(double) * N);
+    orc_grad3(D, H, W, 1, u, gx, gy, gz);
     double e = 0.0;
-    for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x) {
-            size_t o = (size_t)y * W + x;
-            double ax = x + 1 < W ? u[o + 1] - u[o] : 0.0;
-            double ay = y + 1 < H ? u[o + W] - u[o] : 0.0;
-            e += 0.5 * alpha * (u[o] - f[o]) * (u[o] - f[o]) + lam * tv_norm(g_rof_aniso, ax, ay);
-        }
+    for (size_t o = 0; o < N; ++o)
+        e += 0.5 * alpha * (u[o] - f[o]) * (u[o] - f[o]) + lam * tv_norm(aniso, gx[o], gy[o], gz[o]);
+    free(gx); free(gy); free(gz);
     return e;
 }
 
-double orc_rof_direct(int H, int W, const double *f, double alpha, double lam,
-                      double lo, double hi, int iters, double *u)
+/* On a D x H x W volume (D = 1: an image); |grad|^2 <= 4 * (number of axes),
+   so tau = sigma = 1/sqrt(4 * axes) start the accelerated steps. */
+double orc_rof_direct3(int D, int H, int W, const double *f, double alpha, double lam,
+                       double lo, double hi, int iters, int aniso, double *u)
 {
-    size_t N = (size_t)H * W;
+    size_t N = (size_t)D * H * W;
     double *px = (double *)calloc(N, sizeof(double));
     double *py = (double *)calloc(N, sizeof(double));
+    double *pz = (double *)calloc(N, sizeof(double));
     double *ub = (double *)malloc(sizeof(double) * N);
     double *dv = (double *)malloc(sizeof(double) * N);
     double *gx = (double *)malloc(sizeof(double) * N);
     double *gy = (double *)malloc(sizeof(double) * N);
+    double *gz = (double *)malloc(sizeof(double) * N);
     for (size_t o = 0; o < N; ++o) { u[o] = clampd(f[o], lo, hi); ub[o] = u[o]; }
-    double tau = 1.0 / sqrt(8.0), sigma = 1.0 / sqrt(8.0);
+    double axes = D > 1 ? 3.0 : 2.0;
+    double tau = 1.0 / sqrt(4.0 * axes), sigma = 1.0 / sqrt(4.0 * axes);
     for (int n = 0; n < iters; ++n) {
-        orc_grad(H, W, 1, ub, gx, gy);
+        orc_grad3(D, H, W, 1, ub, gx, gy, gz);
         for (size_t o = 0; o < N; ++o) {
             double ax = px[o] + sigma * gx[o], ay = py[o] + sigma * gy[o];
-            tv_project(g_rof_aniso, lam, &ax, &ay);
+            double az = pz[o] + sigma * gz[o];
+            tv_project(aniso, lam, &ax, &ay, &az);
             px[o] = ax;
             py[o] = ay;
+            pz[o] = az;
         }
-        orc_div(H, W, 1, px, py, dv);
+        orc_div3(D, H, W, 1, px, py, pz, dv);
         double theta = 1.0 / sqrt(1.0 + 2.0 * alpha * tau);
         for (size_t o = 0; o < N; ++o) {
             double un = (u[o] + tau * dv[o] + tau * alpha * f[o]) / (1.0 + tau * alpha);
@@ -672,40 +724,46 @@ double orc_rof_direct(int H, int W, const double *f, double alpha, double lam,
     }
     /* gap: primal energy minus the dual objective of the box-constrained
        problem, min_{u in box} alpha/2 (u-f)^2 - u*div p, per pixel */
-    orc_div(H, W, 1, px, py, dv);
+    orc_div3(D, H, W, 1, px, py, pz, dv);
     double dual = 0.0;
     for (size_t o = 0; o < N; ++o) {
         double t = clampd(f[o] + dv[o] / alpha, lo, hi);
         dual += 0.5 * alpha * (t - f[o]) * (t - f[o]) - t * dv[o];
     }
-    double gap = rof_primal(H, W, u, f, alpha, lam) - dual;
-    free(px); free(py); free(ub); free(dv); free(gx); free(gy);
+    double gap = rof_primal(D, H, W, u, f, alpha, lam, aniso) - dual;
+    free(px); free(py); free(pz); free(ub); free(dv); free(gx); free(gy); free(gz);
     return gap;
+}
+
+double orc_rof_energy3(int D, int H, int W, const double *u, const double *f,
+                       double alpha, double lam, int aniso)
+{
+    return rof_primal(D, H, W, u, f, alpha, lam, aniso);
+}
+
+/* Image forms, isotropic |grad u|_2 and anisotropic |grad u|_1. */
+double orc_rof_direct(int H, int W, const double *f, double alpha, double lam,
+                      double lo, double hi, int iters, double *u)
+{
+    return orc_rof_direct3(1, H, W, f, alpha, lam, lo, hi, iters, 0, u);
 }
 
 double orc_rof_energy(int H, int W, const double *u, const double *f,
                       double alpha, double lam)
 {
-    return rof_primal(H, W, u, f, alpha, lam);
+    return rof_primal(1, H, W, u, f, alpha, lam, 0);
 }
 
-/* The same two functions with the anisotropic TV |grad u|_1. */
 double orc_rof_direct_aniso(int H, int W, const double *f, double alpha, double lam,
                             double lo, double hi, int iters, double *u)
 {
-    g_rof_aniso = 1;
-    double g = orc_rof_direct(H, W, f, alpha, lam, lo, hi, iters, u);
-    g_rof_aniso = 0;
-    return g;
+    return orc_rof_direct3(1, H, W, f, alpha, lam, lo, hi, iters, 1, u);
 }
 
 double orc_rof_energy_aniso(int H, int W, const double *u, const double *f,
                             double alpha, double lam)
 {
-    g_rof_aniso = 1;
-    double e = rof_primal(H, W, u, f, alpha, lam);
-    g_rof_aniso = 0;
-    return e;
+    return rof_primal(1, H, W, u, f, alpha, lam, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -755,6 +813,7 @@ int orc_unrolled_grad(const orc_problem *P, int iters, const double *g_u, double
     int H = P->H, W = P->W, k = P->L - 1;
     size_t N = (size_t)H * W, Nk = N * k;
     if (P->kind == ORC_PL) return -2;
+    if (depth(P) > 1) return -3;          /* images only */
     orc_steps S;
     make_steps(P, &S);
     /* stored states: per state u,s,ubar,sbar,v,z,px,py (Nk each) + q (N) */
@@ -778,7 +837,7 @@ int orc_unrolled_grad(const orc_problem *P, int iters, const double *g_u, double
     for (int n = 0; n < iters; ++n) {
         memcpy(ST(n + 1, 0), ST(n, 0), sizeof(double) * per);
         orc_state X = {ST(n + 1, 0), ST(n + 1, 1), ST(n + 1, 2), ST(n + 1, 3), ST(n + 1, 4),
-                       ST(n + 1, 5), ST(n + 1, 6), ST(n + 1, 7), ST(n + 1, 8)};
+                       ST(n + 1, 5), ST(n + 1, 6), ST(n + 1, 7), ST(n + 1, 8), NULL};
         orc_pdhg(P, &X, 1);
     }
     /* seed: dL/du_i = Delta_i dL/du~ */

@@ -32,12 +32,12 @@ class _Problem(C.Structure):
         ("alpha", C.c_double), ("nu", C.c_double),
         ("f", _dp), ("cost", _dp), ("ns", C.c_int),
         ("smin", C.c_double), ("smax", C.c_double), ("theta", C.c_double),
-        ("aniso", C.c_int),
+        ("aniso", C.c_int), ("D", C.c_int),
     ]
 
 
 class _State(C.Structure):
-    _fields_ = [(n, _dp) for n in ("u", "s", "ubar", "sbar", "v", "z", "px", "py", "q")]
+    _fields_ = [(n, _dp) for n in ("u", "s", "ubar", "sbar", "v", "z", "px", "py", "q", "pz")]
 
 
 def build(force: bool = False) -> str:
@@ -70,6 +70,14 @@ def _load():
         lib.orc_grad.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
         lib.orc_div.restype = None
         lib.orc_div.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
+        lib.orc_grad3.restype = None
+        lib.orc_grad3.argtypes = [C.c_int] * 4 + [_dp] * 4
+        lib.orc_div3.restype = None
+        lib.orc_div3.argtypes = [C.c_int] * 4 + [_dp] * 4
+        lib.orc_rof_direct3.restype = C.c_double
+        lib.orc_rof_direct3.argtypes = [C.c_int] * 3 + [_dp] + [C.c_double] * 4 + [C.c_int] * 2 + [_dp]
+        lib.orc_rof_energy3.restype = C.c_double
+        lib.orc_rof_energy3.argtypes = [C.c_int] * 3 + [_dp, _dp, C.c_double, C.c_double, C.c_int]
         lib.orc_steps_get.restype = None
         lib.orc_steps_get.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
         lib.orc_pdhg.restype = C.c_int
@@ -128,17 +136,18 @@ class Problem:
     smax: float = 1.0
     theta: float = 1.0
     aniso: int = 0
+    D: int = 1                  # depth: D > 1 makes a D x H x W volume
     _c: _Problem = field(default=None, repr=False)
 
     def __post_init__(self):
         if self.f is not None:
-            self.f = np.ascontiguousarray(self.f, dtype=np.float64).reshape(self.H * self.W)
+            self.f = np.ascontiguousarray(self.f, dtype=np.float64).reshape(self.N)
         if self.cost is not None:
-            self.cost = np.ascontiguousarray(self.cost, dtype=np.float64).reshape(self.H * self.W, -1)
+            self.cost = np.ascontiguousarray(self.cost, dtype=np.float64).reshape(self.N, -1)
         ns = 0 if self.cost is None else self.cost.shape[1]
         self._c = _Problem(self.kind, self.H, self.W, self.L, self.gmin, self.gmax, self.lam,
                            self.alpha, self.nu, _ptr(self.f), _ptr(self.cost), ns,
-                           self.smin, self.smax, self.theta, self.aniso)
+                           self.smin, self.smax, self.theta, self.aniso, self.D)
 
     @property
     def k(self) -> int:
@@ -146,27 +155,34 @@ class Problem:
 
     @property
     def N(self) -> int:
-        return self.H * self.W
+        return max(self.D, 1) * self.H * self.W
+
+    def with_theta(self, theta: float) -> "Problem":
+        return Problem(self.kind, self.H, self.W, self.L, self.gmin, self.gmax, lam=self.lam,
+                       alpha=self.alpha, nu=self.nu, f=self.f, cost=self.cost, smin=self.smin,
+                       smax=self.smax, theta=theta, aniso=self.aniso, D=self.D)
 
     def ref(self):
         return C.byref(self._c)
 
 
 class State:
-    """PDHG iterate, all variables zero at the start (arrays [pixel, i])."""
+    """PDHG iterate, all variables zero at the start (arrays [pixel, i]);
+    pz, the third component of p_i, is used on volumes only (stays 0)."""
     names = ("u", "s", "ubar", "sbar", "v", "z", "px", "py")
 
     def __init__(self, P: Problem):
         for n in self.names:
             setattr(self, n, np.zeros((P.N, P.k), dtype=np.float64))
         self.q = np.zeros(P.N, dtype=np.float64)
+        self.pz = np.zeros((P.N, P.k), dtype=np.float64)
 
     def _c(self):
-        return _State(*[_ptr(getattr(self, n)) for n in self.names], _ptr(self.q))
+        return _State(*[_ptr(getattr(self, n)) for n in self.names], _ptr(self.q), _ptr(self.pz))
 
     def copy(self, P: Problem) -> "State":
         o = State(P)
-        for n in self.names + ("q",):
+        for n in self.names + ("q", "pz"):
             getattr(o, n)[...] = getattr(self, n)
         return o
 
@@ -209,6 +225,21 @@ def div(H: int, W: int, k: int, px: np.ndarray, py: np.ndarray):
     py = np.ascontiguousarray(py, dtype=np.float64)
     d = np.empty_like(px)
     _load().orc_div(H, W, k, _ptr(px), _ptr(py), _ptr(d))
+    return d
+
+
+def grad3(D: int, H: int, W: int, k: int, u: np.ndarray):
+    """Forward differences (x, y, z) on a D x H x W volume, Neumann."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    gx, gy, gz = np.empty_like(u), np.empty_like(u), np.empty_like(u)
+    _load().orc_grad3(D, H, W, k, _ptr(u), _ptr(gx), _ptr(gy), _ptr(gz))
+    return gx, gy, gz
+
+
+def div3(D: int, H: int, W: int, k: int, px: np.ndarray, py: np.ndarray, pz: np.ndarray):
+    px, py, pz = (np.ascontiguousarray(a, dtype=np.float64) for a in (px, py, pz))
+    d = np.empty_like(px)
+    _load().orc_div3(D, H, W, k, _ptr(px), _ptr(py), _ptr(pz), _ptr(d))
     return d
 
 
@@ -263,6 +294,24 @@ def rof_direct(f: np.ndarray, alpha: float, lam: float, lo: float, hi: float,
     return u, gap
 
 
+def rof_direct3(f: np.ndarray, alpha: float, lam: float, lo: float, hi: float,
+                iters: int, aniso: bool = False) -> tuple[np.ndarray, float]:
+    """The same on a D x H x W volume f; (u, gap)."""
+    D, H, W = f.shape
+    fd = np.ascontiguousarray(f, dtype=np.float64)
+    u = np.empty_like(fd)
+    gap = _load().orc_rof_direct3(D, H, W, _ptr(fd), alpha, lam, lo, hi, iters, int(aniso), _ptr(u))
+    return u, gap
+
+
+def rof_energy3(u: np.ndarray, f: np.ndarray, alpha: float, lam: float,
+                aniso: bool = False) -> float:
+    D, H, W = f.shape
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    fd = np.ascontiguousarray(f, dtype=np.float64)
+    return _load().orc_rof_energy3(D, H, W, _ptr(u), _ptr(fd), alpha, lam, int(aniso))
+
+
 def rof_energy(u: np.ndarray, f: np.ndarray, alpha: float, lam: float,
                aniso: bool = False) -> float:
     H, W = f.shape
@@ -286,13 +335,11 @@ def unrolled_grad(P: Problem, iters: int, g_u: np.ndarray) -> tuple[np.ndarray, 
 def movement(P: Problem, X: State, Xp: State) -> tuple[float, float]:
     """Squared movement of the primal and the dual iterate between two states
     in the metric of the theta = 1 steps: (sum |dx|^2/tau, sum |dy|^2/sigma)."""
-    base = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
-                   f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=1.0, aniso=P.aniso)
-    S = steps(base)
+    S = steps(P.with_theta(1.0))
     dx = (np.sum((X.u - Xp.u) ** 2) / S["tau_u"]
           + np.sum((X.s - Xp.s) ** 2 / S["tau_s"][None, :]))
     dy = (np.sum(((X.v - Xp.v) ** 2 + (X.z - Xp.z) ** 2) / S["sigma_vz"][None, :])
-          + np.sum((X.px - Xp.px) ** 2 + (X.py - Xp.py) ** 2) / S["sigma_p"]
+          + np.sum((X.px - Xp.px) ** 2 + (X.py - Xp.py) ** 2 + (X.pz - Xp.pz) ** 2) / S["sigma_p"]
           + np.sum((X.q - Xp.q) ** 2) / S["sigma_q"])
     return float(dx), float(dy)
 
@@ -305,8 +352,7 @@ def pdhg_adaptive(P: Problem, X: State, checks: int, every: int) -> float:
     th = P.theta if P.theta > 0 else 1.0
     w = 0.5
     for _ in range(checks):
-        Pc = Problem(P.kind, P.H, P.W, P.L, P.gmin, P.gmax, lam=P.lam, alpha=P.alpha, nu=P.nu,
-                     f=P.f, cost=P.cost, smin=P.smin, smax=P.smax, theta=th, aniso=P.aniso)
+        Pc = P.with_theta(th)
         Xp = X.copy(Pc)
         pdhg(Pc, X, every)
         dx, dy = movement(Pc, X, Xp)

@@ -105,6 +105,33 @@ def voronoi_ramps(H: int, W: int, seed: int, cells: int = 24, noise: float = 0.0
     return noisy.reshape(H, W), clean
 
 
+def voronoi_ramps_3d(D: int, H: int, W: int, seed: int, cells: int = 24, noise: float = 0.05,
+                     outliers: float = 0.1) -> tuple[np.ndarray, np.ndarray]:
+    """The volume form of voronoi_ramps: Voronoi cells on seeded sites in a
+    D x H x W box, each a linear ramp a + b x + c y + e z (a ~ U[0.1,0.9],
+    slopes U[-1,1]/512 per voxel) clipped to [0,1]; then N(0, noise^2) and a
+    fraction ``outliers`` of voxels replaced by U[0,1].  Stand-in for a
+    volumetric denoising input (the d = 3 grid of Sec. 4).  Returns (noisy,
+    clean)."""
+    r = Rng(seed, 7)
+    sz, sy, sx = r.uniform(cells, 0, D), r.uniform(cells, 0, H), r.uniform(cells, 0, W)
+    a = r.uniform(cells, 0.1, 0.9)
+    b, c, e = (r.uniform(cells, -1, 1) / 512.0 for _ in range(3))
+    zz, yy, xx = np.mgrid[0:D, 0:H, 0:W].astype(np.float64)
+    lab = np.zeros((D, H, W), dtype=np.int64)
+    best = np.full((D, H, W), np.inf)
+    for j in range(cells):
+        d = (zz - sz[j]) ** 2 + (yy - sy[j]) ** 2 + (xx - sx[j]) ** 2
+        m = d < best
+        best[m] = d[m]
+        lab[m] = j
+    clean = np.clip(a[lab] + b[lab] * xx + c[lab] * yy + e[lab] * zz, 0.0, 1.0)
+    noisy = (clean + r.normal(D * H * W, noise).reshape(D, H, W)).reshape(-1)
+    sel = r.uniform(D * H * W) < outliers
+    noisy[sel] = r.uniform(int(sel.sum()))
+    return noisy.reshape(D, H, W), clean
+
+
 def gradient_noise(H: int, W: int, seed: int, octaves: int = 4, base: float = 64.0) -> np.ndarray:
     """Multi-octave lattice noise with smoothstep interpolation, scaled to [0,1]."""
     r = Rng(seed, 3)
