@@ -77,15 +77,16 @@ extern "C" {
 typedef struct lift_spec {
     int kind;                 /* LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED,
                                  LIFT_PERIODIC_QUAD                         */
-    int H, W;                 /* image size, H*W >= 1                        */
+    int H, W;                 /* image size, H*W >= 1 (one slice of a volume) */
     int L;                    /* labels, 2 <= L <= LIFT_MAX_K + 1            */
     double gamma_min;         /* equidistant labels gamma_1 < ... < gamma_L  */
     double gamma_max;         /*   on [gamma_min, gamma_max] (Sec. 3)         */
     double lambda;            /* TV weight >= 0: ball radius lambda*Delta_i  */
     double alpha, nu;         /* QUAD: alpha > 0.  TRUNC: alpha > 0, nu > 0.
                                  PERIODIC: alpha > 0, nu = period > 0      */
-    const float *f;           /* QUAD/TRUNC: H*W row-major image             */
-    const float *cost;        /* PL: H*W*n_samples, pixel-major              */
+    const float *f;           /* QUAD/TRUNC/PERIODIC: N = D*H*W values,
+                                 voxel (z*H + y)*W + x (an image: z = 0)    */
+    const float *cost;        /* PL: N*n_samples, pixel-major              */
     int n_samples;            /* PL: >= 2                                    */
     double sample_min;        /* PL: sample positions; must cover Gamma      */
     double sample_max;
@@ -100,6 +101,13 @@ typedef struct lift_spec {
                                  balls, Prop. 5); 1: anisotropic |nu|_1
                                  (K = l-infinity boxes |p_i|_inf <= lambda
                                  Delta, Sec. 5.3)                          */
+    int D;                    /* depth: D > 1 makes the domain a D x H x W
+                                 volume (the d = 3 Cartesian grid of Sec. 4:
+                                 three forward differences, p_i in R^3, and
+                                 tau_u = theta/7 instead of theta/5); 0 or 1
+                                 is an image.  D*H*W*(L-1) < 2^31.  Batches,
+                                 the unrolled solve and lift_energy_noalloc
+                                 take images only (LIFT_ERR_SPEC).          */
 } lift_spec;
 
 typedef struct lift_ctx *lift_handle;
@@ -178,16 +186,19 @@ int lift_energy(lift_handle h, double *primal_relaxed, double *dual,
 int lift_gap(lift_handle h, double *rel_gap);
 
 /* lift_unlift: u~(x) = gamma_1 + sum_i clamp(u_i(x), 0, 1) Delta_i (the
- * layer-cake formula of Sec. 3) into out[H*W] (row-major), a device pointer
+ * layer-cake formula of Sec. 3) into out[N] (N = D*H*W, voxel order of f), a
+ * device pointer
  * (on_host = 0, asynchronous) or a host pointer (on_host = 1). */
 int lift_unlift(lift_handle h, float *out, int on_host);
 
 /* State image for checkpoint / resume and for tests.  Layout (bytes, in
- * this order, all float32, pixel p = y*W + x, interval i = 0..k-1):
- *   primal  [H*W][k] float2 {u_i, s_i}
- *   xbar    [H*W][k] float2 {ubar_i, sbar_i}   (extrapolated primal)
- *   dual    [H*W][k] float4 {v_i, z_i, px_i, py_i}
- *   q       [H*W]    float
+ * this order, all float32, pixel p = (z*H + y)*W + x, N = D*H*W, interval
+ * i = 0..k-1):
+ *   primal  [N][k] float2 {u_i, s_i}
+ *   xbar    [N][k] float2 {ubar_i, sbar_i}   (extrapolated primal)
+ *   dual    [N][k] float4 {v_i, z_i, px_i, py_i}
+ *   q       [N]    float
+ *   pz      [N][k] float  (volumes only: the z component of p_i)
  * lift_state_bytes returns the total size.  get/set copy exactly that many
  * bytes (bytes must equal it, else LIFT_ERR_ARG). */
 size_t lift_state_bytes(lift_handle h);

@@ -75,8 +75,8 @@ int dev_alloc(void **p, size_t bytes)
 void free_ctx(lift_ctx *h)
 {
     if (!h) return;
-    void *ptrs[] = {h->S.x, h->S.xbar, h->S.y, h->S.q, h->icst, h->f, h->cost, h->rhat,
-                    h->bpos, h->bstart, h->ubuf, h->partial, h->dout};
+    void *ptrs[] = {h->S.x, h->S.xbar, h->S.y, h->S.q, h->S.pz, h->icst, h->f, h->cost,
+                    h->rhat, h->bpos, h->bstart, h->ubuf, h->partial, h->dout};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ckpt) cudaFree(h->ckpt);
@@ -97,9 +97,9 @@ bool is_finite(double x) { return std::isfinite(x); }
 int validate(const lift_spec *s)
 {
     if (s->kind < LIFT_QUAD || s->kind > LIFT_PERIODIC_QUAD) return LIFT_ERR_SPEC;
-    if (s->H < 1 || s->W < 1) return LIFT_ERR_SPEC;
+    if (s->H < 1 || s->W < 1 || s->D < 0) return LIFT_ERR_SPEC;
     if (s->L < 2 || s->L > LIFT_MAX_K + 1) return LIFT_ERR_SPEC;
-    const long long N = static_cast<long long>(s->H) * s->W;
+    const long long N = static_cast<long long>(std::max(s->D, 1)) * s->H * s->W;
     if (N * (s->L - 1) > (1LL << 31) - 1) return LIFT_ERR_SPEC;
     if (!is_finite(s->gamma_min) || !is_finite(s->gamma_max) || !(s->gamma_max > s->gamma_min))
         return LIFT_ERR_SPEC;
@@ -174,7 +174,10 @@ void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<
                             static_cast<float>(sig), static_cast<float>(spec->lambda * d));
     }
     P = LiftParams{};
-    P.H = spec->H; P.W = spec->W; P.k = k; P.N = spec->H * spec->W;
+    P.D = std::max(spec->D, 1);
+    P.H = spec->H; P.W = spec->W; P.k = k;
+    P.HW = spec->H * spec->W;
+    P.N = P.D * P.HW;
     P.kind = spec->kind;
     P.aniso = spec->tv_anisotropic ? 1 : 0;
     P.ppb = threads / k;
@@ -189,6 +192,11 @@ void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<
         while ((1LL << l) < spec->W) ++l;
         P.wshift = 31 + l;
         P.wmul = ((1ULL << P.wshift) / static_cast<unsigned long long>(spec->W)) + 1ULL;
+        // the same for the slice of a global row index, row / H
+        l = 0;
+        while ((1LL << l) < spec->H) ++l;
+        P.hshift = 31 + l;
+        P.hmul = ((1ULL << P.hshift) / static_cast<unsigned long long>(spec->H)) + 1ULL;
     }
     P.gmin = static_cast<float>(spec->gamma_min);
     P.lam = static_cast<float>(spec->lambda);
@@ -196,7 +204,8 @@ void make_params(const lift_spec *spec, int threads, LiftParams &P, std::vector<
     P.inv_alpha = spec->alpha > 0.0 ? static_cast<float>(1.0 / spec->alpha) : 0.0f;
     P.nu = static_cast<float>(spec->nu);
     P.wtrunc = spec->kind == LIFT_TRUNC_QUAD ? static_cast<float>(sqrt(spec->nu / spec->alpha)) : 0.0f;
-    P.tau_u = static_cast<float>(0.2 * th);
+    // the column of u holds 1 + 2d entries: 1 + 4 on an image, 1 + 6 on a volume
+    P.tau_u = static_cast<float>(th / (P.D > 1 ? 7.0 : 5.0));
     P.sigma_q = static_cast<float>(1.0 / (th * (gL - label(spec, 0))));
     P.sigma_p = static_cast<float>(0.5 / th);
 }
@@ -249,6 +258,10 @@ int save_prev(lift_handle h)
                             cudaMemcpyDeviceToDevice, h->stream));
     LIFT_CK(cudaMemcpyAsync(b + 2 * Nk * sizeof(float2) + Nk * sizeof(float4), h->S.q,
                             h->N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->S.pz)
+        LIFT_CK(cudaMemcpyAsync(b + 2 * Nk * sizeof(float2) + Nk * sizeof(float4) +
+                                    h->N * sizeof(float),
+                                h->S.pz, Nk * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     h->prev_valid = true;
     return LIFT_OK;
 }
@@ -266,6 +279,7 @@ int rebalance(lift_handle h)
     Sp.xbar = nullptr;
     Sp.y = reinterpret_cast<float4 *>(h->prev + 2 * Nk * sizeof(float2));
     Sp.q = reinterpret_cast<float *>(h->prev + 2 * Nk * sizeof(float2) + Nk * sizeof(float4));
+    Sp.pz = h->S.pz ? Sp.q + h->N : nullptr;
     LIFT_CK(lift::launch_movement(h->P, h->S, Sp, static_cast<float>(h->theta), h->partial, h->dout,
                                   h->stream));
     LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 3 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -298,7 +312,7 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     h->H = spec->H;
     h->W = spec->W;
     h->k = spec->L - 1;
-    h->N = spec->H * spec->W;
+    h->N = std::max(spec->D, 1) * spec->H * spec->W;
     h->check_every = spec->check_every > 0 ? spec->check_every : 100;
     const int k = h->k;
     const size_t N = static_cast<size_t>(h->N), Nk = N * k;
@@ -337,6 +351,7 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     ALLOC(h->S.xbar, Nk * sizeof(float2));
     ALLOC(h->S.y, Nk * sizeof(float4));
     ALLOC(h->S.q, N * sizeof(float));
+    if (P.D > 1) ALLOC(h->S.pz, Nk * sizeof(float));
     ALLOC(h->icst, k * sizeof(float4));
     ALLOC(h->ubuf, N * sizeof(float));
     ALLOC(h->partial, 3 * sizeof(double) * lift::energy_blocks(P));
@@ -404,6 +419,7 @@ int lift_reset(lift_handle h)
     LIFT_CK(cudaMemsetAsync(h->S.xbar, 0, Nk * sizeof(float2), h->stream));
     LIFT_CK(cudaMemsetAsync(h->S.y, 0, Nk * sizeof(float4), h->stream));
     LIFT_CK(cudaMemsetAsync(h->S.q, 0, h->N * sizeof(float), h->stream));
+    if (h->S.pz) LIFT_CK(cudaMemsetAsync(h->S.pz, 0, Nk * sizeof(float), h->stream));
     h->prev_valid = false;
     h->adapt_w = 0.5;
     return LIFT_OK;
@@ -567,20 +583,22 @@ size_t lift_state_bytes(lift_handle h)
 {
     if (!h) return 0;
     const size_t Nk = static_cast<size_t>(h->N) * h->k;
-    return Nk * (2 * sizeof(float2) + sizeof(float4)) + h->N * sizeof(float);
+    return Nk * (2 * sizeof(float2) + sizeof(float4)) + h->N * sizeof(float) +
+           (h->S.pz ? Nk * sizeof(float) : 0);
 }
 
 static int copy_state(lift_handle h, char *hostdev, size_t bytes, int on_host, bool get)
 {
     if (!h || !hostdev || bytes != lift_state_bytes(h)) return LIFT_ERR_ARG;
     const size_t Nk = static_cast<size_t>(h->N) * h->k;
-    void *parts[4] = {h->S.x, h->S.xbar, h->S.y, h->S.q};
-    const size_t sizes[4] = {Nk * sizeof(float2), Nk * sizeof(float2), Nk * sizeof(float4),
-                             h->N * sizeof(float)};
+    void *parts[5] = {h->S.x, h->S.xbar, h->S.y, h->S.q, h->S.pz};
+    const size_t sizes[5] = {Nk * sizeof(float2), Nk * sizeof(float2), Nk * sizeof(float4),
+                             h->N * sizeof(float), Nk * sizeof(float)};
+    const int nparts = h->S.pz ? 5 : 4;
     cudaMemcpyKind kind = on_host ? (get ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice)
                                   : cudaMemcpyDeviceToDevice;
     size_t off = 0;
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < nparts; ++j) {
         if (get)
             LIFT_CK(cudaMemcpyAsync(hostdev + off, parts[j], sizes[j], kind, h->stream));
         else
@@ -782,6 +800,7 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
         const int rc = validate(&specs[j]);
         if (rc != LIFT_OK) return rc;
         if (specs[j].kind == LIFT_PL_SAMPLED || specs[j].kind != specs[0].kind) return LIFT_ERR_SPEC;
+        if (specs[j].D > 1) return LIFT_ERR_SPEC;      // images only
     }
     lift_batch b = new (std::nothrow) lift_batch_ctx();
     if (!b) return LIFT_ERR_OOM;
@@ -1143,7 +1162,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
 int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every)
 {
     if (!h || iters < 1 || checkpoint_every < 1) return LIFT_ERR_ARG;
-    if (h->kind == LIFT_PL_SAMPLED) return LIFT_ERR_SPEC;
+    if (h->kind == LIFT_PL_SAMPLED || h->P.D > 1) return LIFT_ERR_SPEC;
     const size_t sb = state_stride(h);
     const int nck = (iters + checkpoint_every - 1) / checkpoint_every;
     if (nck > h->ckpt_count) {

@@ -11,7 +11,10 @@
 namespace lift {
 
 struct LiftParams {
-    int H, W, k, N;          // image size, intervals, pixels
+    int H, W, k, N;          // image size, intervals, pixels (voxels: D*H*W)
+    int D, HW;               // depth (1: an image) and slice size H*W
+    unsigned long long hmul; // slice = (row * hmul) >> hshift for row = pix / W,
+    int hshift;              // exact for row < 2^31 (volumes only)
     int kind;                // 0 quadratic, 1 truncated quadratic, 2 PL
     int aniso;               // 1: anisotropic TV (box projection of p_i)
     int ppb;                 // pixels per 256-thread tile in the step kernels
@@ -43,6 +46,7 @@ struct LiftState {
     float2 *xbar;   // [N][k] {ubar, sbar}
     float4 *y;      // [N][k] {v, z, px, py}
     float *q;       // [N]
+    float *pz;      // [N][k] third component of p_i (volumes; null on images)
 };
 
 // One instance of a batch: its parameters, its state and its first tile in

@@ -24,7 +24,9 @@
 // for the pixels that straddle a warp boundary.  Halo values (ubar at x+1
 // and y+1 in the dual step, p at x-1 and y-1 in the primal step) are re-read
 // from L1/L2; the algorithmic DRAM traffic is (20k + 3) floats per pixel and
-// iteration (+ f).
+// iteration (+ f).  On a volume (D > 1, the d = 3 grid of Sec. 4) p_i has a
+// third component, kept in its own [N][k] float array pz, and the
+// differences add the next / previous slice: (23k + 3) floats per voxel.
 #include "lift_device.cuh"
 #include "lift_params.h"
 
@@ -41,6 +43,13 @@ __device__ __forceinline__ void split_thread(const LiftParams &P, int tid, int &
 __device__ __forceinline__ int pixel_row(const LiftParams &P, int pix)
 {
     return static_cast<int>((static_cast<unsigned long long>(pix) * P.wmul) >> P.wshift);
+}
+
+// Row within its slice of a global row index z*H + y (volumes).
+__device__ __forceinline__ int row_in_slice(const LiftParams &P, int row)
+{
+    const int zz = static_cast<int>((static_cast<unsigned long long>(row) * P.hmul) >> P.hshift);
+    return row - zz * P.H;
 }
 
 // Inclusive prefix sum of `val` over the thread's pixel segment
@@ -132,10 +141,13 @@ __device__ __forceinline__ SegScan2 block_segmented_scan2(float2 val, int seg, i
     return r;
 }
 
-template <int KIND, int THREADS>
+// VOL: a D x H x W volume, whose p_i has a third component in pz (Sec. 4 on
+// the d = 3 grid); images take VOL = false and never touch pz.
+template <int KIND, int THREADS, bool VOL = false>
 __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__restrict__ xbar,
                                           float4 *__restrict__ y, float *__restrict__ q,
-                                          int tile, float *s_in, float *s_last)
+                                          int tile, float *s_in, float *s_last,
+                                          float *__restrict__ pz = nullptr)
 {
     const int tid = threadIdx.x;
     int lp, i;
@@ -155,24 +167,34 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
 
     const int row = pixel_row(P, pix);
     const int col = pix - row * P.W;
+    const int yy = VOL ? row_in_slice(P, row) : row;
     const float4 ic = __ldg(P.icst + i);      // {gamma_i, tau_s, sigma_vz, lambda*Delta}
 
     // TV dual: forward differences (Neumann), ascent, l2-ball projection
     const float gx = col + 1 < P.W ? xbar[o + P.k].x - xb.x : 0.0f;
-    const float gy = row + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
+    const float gy = yy + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
     float px = d.z + P.sigma_p * gx;
     float py = d.w + P.sigma_p * gy;
+    float pzv = 0.0f;
+    if (VOL) {
+        const float gz = pix < P.N - P.HW ? xbar[o + static_cast<size_t>(P.HW) * P.k].x - xb.x
+                                          : 0.0f;
+        pzv = pz[o] + P.sigma_p * gz;
+    }
     if (P.aniso) {                              // l-infinity box (anisotropic TV)
         px = fminf(fmaxf(px, -ic.w), ic.w);
         py = fminf(fmaxf(py, -ic.w), ic.w);
+        if (VOL) pzv = fminf(fmaxf(pzv, -ic.w), ic.w);
     } else {                                    // l2 ball (isotropic TV)
-        const float n2 = px * px + py * py;
+        const float n2 = px * px + py * py + (VOL ? pzv * pzv : 0.0f);
         if (n2 > ic.w * ic.w) {
             const float sc2 = ic.w * rsqrtf(n2);
             px *= sc2;
             py *= sc2;
+            if (VOL) pzv *= sc2;
         }
     }
+    if (VOL) pz[o] = pzv;
 
     // data duals: sum of sbar over the pixel's later intervals = total - inclusive
     const float tail = sc.total - sc.incl;
@@ -231,23 +253,25 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
 }
 
-template <int KIND>
+template <int KIND, bool VOL>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
-                 float *__restrict__ q)
+                 float *__restrict__ q, float *__restrict__ pz)
 {
     __shared__ float s_in[kStepThreads];
     __shared__ float s_last[kStepThreads / 32];
     if (P.live != nullptr && *P.live == 0) return;
-    dual_tile<KIND, kStepThreads>(P, xbar, y, q, blockIdx.x, s_in, s_last);
+    dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x, s_in, s_last, pz);
 }
 
 // Single-instance primal step: each block takes two consecutive tiles and
 // issues the loads of both before the (shared) scan, doubling the bytes in
 // flight per thread; the primal step waits on memory rather than on issue.
+template <bool VOL>
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
-                   const float4 *__restrict__ y, const float *__restrict__ q)
+                   const float4 *__restrict__ y, const float *__restrict__ q,
+                   const float *__restrict__ pz)
 {
     __shared__ float2 s_in[kStepThreads];
     __shared__ float2 s_last[kStepThreads / 32];
@@ -273,12 +297,17 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
         if (!act[u]) continue;
         const int row = pixel_row(P, pix[u]);
         const int col = pix[u] - row * P.W;
+        const int yy = VOL ? row_in_slice(P, row) : row;
         const float qq = q[pix[u]];
         float dv = 0.0f;
         if (col + 1 < P.W) dv += d[u].z;
         if (col > 0) dv -= y[o[u] - P.k].z;
-        if (row + 1 < P.H) dv += d[u].w;
-        if (row > 0) dv -= y[o[u] - static_cast<size_t>(P.W) * P.k].w;
+        if (yy + 1 < P.H) dv += d[u].w;
+        if (yy > 0) dv -= y[o[u] - static_cast<size_t>(P.W) * P.k].w;
+        if (VOL) {
+            if (pix[u] < P.N - P.HW) dv += pz[o[u]];
+            if (pix[u] >= P.HW) dv -= pz[o[u] - static_cast<size_t>(P.HW) * P.k];
+        }
         const float head = (u == 0 ? sc.incl.x : sc.incl.y) - d[u].x;
         const float un = fminf(fmaxf(xo[u].x - P.tau_u * (d[u].x - dv), 0.0f), 1.0f);
         const float sn = xo[u].y - ic.y * (d[u].y - P.delta * qq + P.delta * head - ic.x * d[u].x);
@@ -367,17 +396,24 @@ static inline int step_blocks(const LiftParams &P)
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
 {
     const int nb = step_blocks(P);
-    if (P.kind == 2)
-        dual_step_kernel<2><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
-    else
-        dual_step_kernel<0><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+    const bool vol = P.D > 1;
+    if (P.kind == 2) {
+        if (vol) dual_step_kernel<2, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
+        else dual_step_kernel<2, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+    } else {
+        if (vol) dual_step_kernel<0, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
+        else dual_step_kernel<0, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
 {
-    primal_step_kernel<<<(step_blocks(P) + 1) / 2, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y,
-                                                                        S.q);
+    const int nb = (step_blocks(P) + 1) / 2;
+    if (P.D > 1)
+        primal_step_kernel<true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz);
+    else
+        primal_step_kernel<false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
     return cudaGetLastError();
 }
 

@@ -109,19 +109,24 @@ __device__ __forceinline__ float unlift_pixel(const float2 *__restrict__ x, int 
     return gmin + delta * a;
 }
 
-template <int KIND>
+// VOL: a D x H x W volume; p_i's third component in pz, and the slice
+// neighbours (z + 1 for the forward differences, z - 1 in div p) join.
+template <int KIND, bool VOL>
 __global__ void __launch_bounds__(kEnergyThreads)
 energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__restrict__ y,
-              double *__restrict__ partial)
+              const float *__restrict__ pz, double *__restrict__ partial)
 {
     const int pix = blockIdx.x * kEnergyThreads + threadIdx.x;
     double eP = 0.0, eD = 0.0, eE = 0.0;
     if (pix < P.N) {
         const int k = P.k;
         const int row = pix / P.W, col = pix - row * P.W;
+        const int yy = VOL ? row % P.H : row;
         const size_t o = static_cast<size_t>(pix) * k;
         const size_t sx = static_cast<size_t>(k), sy = static_cast<size_t>(P.W) * k;
-        const bool hr = col + 1 < P.W, hd = row + 1 < P.H, hl = col > 0, hu = row > 0;
+        const size_t sz = static_cast<size_t>(P.HW) * k;
+        const bool hr = col + 1 < P.W, hd = yy + 1 < P.H, hl = col > 0, hu = yy > 0;
+        const bool hb = VOL && pix < P.N - P.HW, hf = VOL && pix >= P.HW;
 
         // dual bound: sum_i min(0, v_i - div p_i) - max_i (c_i(v) + rho_i^*(v_i/Delta))
         double dsum = 0.0, prefix = 0.0, cmax = -INFINITY;
@@ -132,6 +137,8 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
             if (hl) dv -= y[o + i - sx].z;
             if (hd) dv += d.w;
             if (hu) dv -= y[o + i - sy].w;
+            if (hb) dv += pz[o + i];
+            if (hf) dv -= pz[o + i - sz];
             const float g = d.x - dv;
             dsum += g < 0.0f ? static_cast<double>(g) : 0.0;
             const float gi = P.gmin + P.delta * i;
@@ -145,9 +152,11 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
 
         // primal bound on the monotone projection of u
         float w[LIFT_MAXK_DEV], wr[LIFT_MAXK_DEV], wd[LIFT_MAXK_DEV];
+        float wb[VOL ? LIFT_MAXK_DEV : 1];
         monotone_project(x + o, k, w);
         if (hr) monotone_project(x + o + sx, k, wr);
         if (hd) monotone_project(x + o + sy, k, wd);
+        if (VOL && hb) monotone_project(x + o + sz, k, wb);
         double dat = 0.0, tv = 0.0;
         float tail = 0.0f;
         float Snext = 0.0f;                      // S_{i+1}, starting from S_k = 0
@@ -167,8 +176,9 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
             }
             const float ax = hr ? wr[i] - w[i] : 0.0f;
             const float ay = hd ? wd[i] - w[i] : 0.0f;
-            tv += static_cast<double>(P.delta * (P.aniso ? fabsf(ax) + fabsf(ay)
-                                                         : sqrtf(ax * ax + ay * ay)));
+            const float az = VOL && hb ? wb[VOL ? i : 0] - w[i] : 0.0f;
+            tv += static_cast<double>(P.delta * (P.aniso ? fabsf(ax) + fabsf(ay) + fabsf(az)
+                                                         : sqrtf(ax * ax + ay * ay + az * az)));
             Snext = Si;
         }
         eP = dat + static_cast<double>(P.lam) * tv;
@@ -177,9 +187,11 @@ energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__
         const float ut = unlift_pixel(x + o, k, P.gmin, P.delta);
         const float ax = hr ? unlift_pixel(x + o + sx, k, P.gmin, P.delta) - ut : 0.0f;
         const float ay = hd ? unlift_pixel(x + o + sy, k, P.gmin, P.delta) - ut : 0.0f;
+        const float az = hb ? unlift_pixel(x + o + sz, k, P.gmin, P.delta) - ut : 0.0f;
         eE = static_cast<double>(data_rho(P, pix, ut)) +
              static_cast<double>(P.lam) *
-                 static_cast<double>(P.aniso ? fabsf(ax) + fabsf(ay) : sqrtf(ax * ax + ay * ay));
+                 static_cast<double>(P.aniso ? fabsf(ax) + fabsf(ay) + fabsf(az)
+                                             : sqrtf(ax * ax + ay * ay + az * az));
     }
 
     // block reduction: warp shuffles, then one value per warp
@@ -234,10 +246,14 @@ cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *parti
                           cudaStream_t st)
 {
     const int nb = energy_blocks(P);
-    if (P.kind == 2)
-        energy_kernel<2><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, partial);
-    else
-        energy_kernel<0><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, partial);
+    const bool vol = P.D > 1;
+    if (P.kind == 2) {
+        if (vol) energy_kernel<2, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial);
+        else energy_kernel<2, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial);
+    } else {
+        if (vol) energy_kernel<0, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial);
+        else energy_kernel<0, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     energy_finish_kernel<<<1, kEnergyThreads, 0, st>>>(partial, nb, out);
@@ -251,8 +267,9 @@ cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *parti
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEnergyThreads)
 movement_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__restrict__ y,
-                const float *__restrict__ q, const float2 *__restrict__ xp,
-                const float4 *__restrict__ yp, const float *__restrict__ qp, float theta,
+                const float *__restrict__ q, const float *__restrict__ pz,
+                const float2 *__restrict__ xp, const float4 *__restrict__ yp,
+                const float *__restrict__ qp, const float *__restrict__ pzp, float theta,
                 double *__restrict__ partial)
 {
     const int pix = blockIdx.x * kEnergyThreads + threadIdx.x;
@@ -268,7 +285,9 @@ movement_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *
             mx += static_cast<double>(du * du * itu + ds * ds * (theta / ic.y));
             const float4 c = y[o + i], e = yp[o + i];
             const float dv = c.x - e.x, dz = c.y - e.y, dpx = c.z - e.z, dpy = c.w - e.w;
-            my += static_cast<double>((dv * dv + dz * dz) / (ic.z * theta) + (dpx * dpx + dpy * dpy) * isp);
+            const float dpz = pz != nullptr ? pz[o + i] - pzp[o + i] : 0.0f;
+            my += static_cast<double>((dv * dv + dz * dz) / (ic.z * theta) +
+                                      (dpx * dpx + dpy * dpy + dpz * dpz) * isp);
         }
         const float dq = q[pix] - qp[pix];
         my += static_cast<double>(dq * dq / (P.sigma_q * theta));
@@ -294,8 +313,8 @@ cudaError_t launch_movement(const LiftParams &P, const LiftState &S, const LiftS
                             float theta, double *partial, double *out, cudaStream_t st)
 {
     const int nb = energy_blocks(P);
-    movement_kernel<<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.q, Sprev.x, Sprev.y, Sprev.q,
-                                                   theta, partial);
+    movement_kernel<<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.q, S.pz, Sprev.x, Sprev.y,
+                                                   Sprev.q, Sprev.pz, theta, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     energy_finish_kernel<<<1, kEnergyThreads, 0, st>>>(partial, nb, out);
@@ -410,6 +429,7 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
     if (!(spec->gamma_max > spec->gamma_min) || !(spec->lambda >= 0.0) || !(spec->alpha > 0.0))
         return LIFT_ERR_SPEC;
     if (spec->kind == LIFT_TRUNC_QUAD && !(spec->nu > 0.0)) return LIFT_ERR_SPEC;
+    if (spec->D > 1) return LIFT_ERR_SPEC;                 // images only
     const long long npix = static_cast<long long>(spec->H) * spec->W;
     if (npix > LIFT_NOALLOC_MAX_PIXELS) return LIFT_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(state) & 15u) != 0) return LIFT_ERR_ARG;
@@ -432,6 +452,7 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
     lift::LiftParams P{};
     const int k = spec->L - 1;
     P.H = spec->H; P.W = spec->W; P.k = k; P.N = static_cast<int>(npix);
+    P.D = 1; P.HW = P.N;
     P.kind = spec->kind;
     P.aniso = spec->tv_anisotropic ? 1 : 0;
     P.delta = static_cast<float>((spec->gamma_max - spec->gamma_min) / k);
@@ -448,7 +469,7 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
                                                         2 * Nk * sizeof(float2));
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nb = lift::energy_blocks(P);
-    lift::energy_kernel<0><<<nb, lift::kEnergyThreads, 0, st>>>(P, x, y, scratch);
+    lift::energy_kernel<0, false><<<nb, lift::kEnergyThreads, 0, st>>>(P, x, y, nullptr, scratch);
     if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;
     lift::energy_finish_kernel<<<1, lift::kEnergyThreads, 0, st>>>(scratch, nb, out);
     if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;

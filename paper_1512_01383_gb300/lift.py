@@ -43,7 +43,7 @@ class lift_spec(C.Structure):
         ("f", C.c_void_p), ("cost", C.c_void_p), ("n_samples", C.c_int),
         ("sample_min", C.c_double), ("sample_max", C.c_double),
         ("data_on_host", C.c_int), ("check_every", C.c_int), ("step_balance", C.c_double),
-        ("adaptive_balance", C.c_int), ("tv_anisotropic", C.c_int),
+        ("adaptive_balance", C.c_int), ("tv_anisotropic", C.c_int), ("D", C.c_int),
     ]
 
 
@@ -252,7 +252,8 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
               lam: float, alpha: float = 1.0, nu: float = 0.0, f=None, cost=None,
               sample_min: float = 0.0, sample_max: float = 1.0,
               check_every: int = 100, step_balance: float = 1.0,
-              adaptive_balance: bool = False, anisotropic: bool = False) -> lift_spec:
+              adaptive_balance: bool = False, anisotropic: bool = False,
+              depth: int = 1) -> lift_spec:
     data = f if kind != LIFT_PL_SAMPLED else cost
     p, on_host = _ptr(data)
     n_samples = 0
@@ -261,22 +262,24 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
     return lift_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu,
                      p if kind != LIFT_PL_SAMPLED else 0, p if kind == LIFT_PL_SAMPLED else 0,
                      n_samples, sample_min, sample_max, on_host, check_every, step_balance,
-                     1 if adaptive_balance else 0, 1 if anisotropic else 0)
+                     1 if adaptive_balance else 0, 1 if anisotropic else 0, depth)
 
 
 class Solver:
-    """A lifted problem on the GPU: ``Solver(kind, H, W, L, ...)``."""
+    """A lifted problem on the GPU: ``Solver(kind, H, W, L, ...)``; depth > 1
+    makes it a depth x H x W volume."""
 
     def __init__(self, kind: int, H: int, W: int, L: int, gamma_min: float = 0.0,
                  gamma_max: float = 1.0, lam: float = 0.0, alpha: float = 1.0,
                  nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
                  sample_max: float = 1.0, check_every: int = 100, stream: int | None = None,
                  step_balance: float = 1.0, adaptive_balance: bool = False,
-                 anisotropic: bool = False):
+                 anisotropic: bool = False, depth: int = 1):
         self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
+        self.D = max(int(depth), 1)
         self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
                               sample_min, sample_max, check_every, step_balance, adaptive_balance,
-                              anisotropic)
+                              anisotropic, depth)
         self._keep = (f, cost)
         self.h = lift_create(self.spec, stream)
         self._keep = None
@@ -316,9 +319,14 @@ class Solver:
     def gap(self):
         return lift_gap(self.h)
 
+    @property
+    def N(self) -> int:
+        return self.D * self.H * self.W
+
     def unlift(self, out=None) -> np.ndarray:
         if out is None:
-            out = np.empty((self.H, self.W), dtype=np.float32)
+            shape = (self.H, self.W) if self.D == 1 else (self.D, self.H, self.W)
+            out = np.empty(shape, dtype=np.float32)
         lift_unlift(self.h, out)
         return out
 
@@ -327,23 +335,29 @@ class Solver:
         nb = lift_state_bytes(self.h)
         buf = np.empty(nb, dtype=np.uint8)
         lift_get_state(self.h, buf)
-        N, k = self.H * self.W, self.k
+        N, k = self.N, self.k
         f = buf.view(np.float32)
         o = 0
         x = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
         xb = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
         y = f[o:o + 4 * N * k].reshape(N, k, 4); o += 4 * N * k
-        q = f[o:o + N]
-        return {"u": x[..., 0], "s": x[..., 1], "ubar": xb[..., 0], "sbar": xb[..., 1],
-                "v": y[..., 0], "z": y[..., 1], "px": y[..., 2], "py": y[..., 3], "q": q}
+        q = f[o:o + N]; o += N
+        st = {"u": x[..., 0], "s": x[..., 1], "ubar": xb[..., 0], "sbar": xb[..., 1],
+              "v": y[..., 0], "z": y[..., 1], "px": y[..., 2], "py": y[..., 3], "q": q}
+        if self.D > 1:
+            st["pz"] = f[o:o + N * k].reshape(N, k)
+        return st
 
     def set_state(self, st: dict):
-        N, k = self.H * self.W, self.k
+        N, k = self.N, self.k
         x = np.stack([st["u"], st["s"]], -1).astype(np.float32).reshape(-1)
         xb = np.stack([st["ubar"], st["sbar"]], -1).astype(np.float32).reshape(-1)
         y = np.stack([st["v"], st["z"], st["px"], st["py"]], -1).astype(np.float32).reshape(-1)
         q = np.asarray(st["q"], dtype=np.float32).reshape(N)
-        buf = np.ascontiguousarray(np.concatenate([x, xb, y, q]))
+        parts = [x, xb, y, q]
+        if self.D > 1:
+            parts.append(np.asarray(st["pz"], dtype=np.float32).reshape(-1))
+        buf = np.ascontiguousarray(np.concatenate(parts))
         assert buf.size * 4 == lift_state_bytes(self.h) and N * k > 0
         lift_set_state(self.h, buf)
 

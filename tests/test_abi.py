@@ -65,7 +65,8 @@ def _spec(lib, **kw):
 @pytest.mark.parametrize("bad", [
     dict(kind=7), dict(H=0), dict(W=-1), dict(L=1), dict(L=66), dict(gamma_max=0.0),
     dict(lam=-1.0), dict(alpha=0.0), dict(nu=0.0), dict(lam=float("nan")),
-    dict(alpha=float("inf")), dict(f=None),
+    dict(alpha=float("inf")), dict(f=None), dict(depth=-1),
+    dict(H=4096, W=4096, L=65, depth=2),          # N*k beyond 2^31
 ])
 def test_invalid_spec_rejected_before_any_cuda_call(lib, bad):
     s, keep = _spec(lib, **bad)
@@ -100,3 +101,11 @@ def test_null_arguments(lib):
     assert L.lift_batch_schedule(None, None, None, None) == lib.LIFT_ERR_ARG
     assert L.lift_batch_size(None) == 0
     L.lift_batch_destroy(None)
+
+
+def test_volume_batch_rejected_before_any_cuda_call(lib):
+    s, keep = _spec(lib, depth=2)
+    arr = (lib.lift_spec * 1)(s)
+    b = C.c_void_p()
+    assert lib.load().lift_create_batch(arr, 1, None, C.byref(b)) == lib.LIFT_ERR_SPEC
+    assert not b.value
