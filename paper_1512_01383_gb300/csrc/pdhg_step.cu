@@ -253,21 +253,22 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
 }
 
-template <int KIND, bool VOL>
+// LIVE: a batch member, whose blocks return while its live flag is 0.
+template <int KIND, bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
                  float *__restrict__ q, float *__restrict__ pz)
 {
     __shared__ float s_in[kStepThreads];
     __shared__ float s_last[kStepThreads / 32];
-    if (P.live != nullptr && *P.live == 0) return;
+    if (LIVE && *P.live == 0) return;
     dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x, s_in, s_last, pz);
 }
 
 // Single-instance primal step: each block takes two consecutive tiles and
 // issues the loads of both before the (shared) scan, doubling the bytes in
 // flight per thread; the primal step waits on memory rather than on issue.
-template <bool VOL>
+template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q,
@@ -275,7 +276,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
 {
     __shared__ float2 s_in[kStepThreads];
     __shared__ float2 s_last[kStepThreads / 32];
-    if (P.live != nullptr && *P.live == 0) return;
+    if (LIVE && *P.live == 0) return;
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
@@ -395,14 +396,17 @@ static inline int step_blocks(const LiftParams &P)
 
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
 {
+    // volumes never belong to a batch, so VOL and LIVE do not meet
     const int nb = step_blocks(P);
-    const bool vol = P.D > 1;
+    const bool vol = P.D > 1, live = P.live != nullptr;
     if (P.kind == 2) {
-        if (vol) dual_step_kernel<2, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-        else dual_step_kernel<2, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+        if (vol) dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
+        else if (live) dual_step_kernel<2, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+        else dual_step_kernel<2, false, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
     } else {
-        if (vol) dual_step_kernel<0, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-        else dual_step_kernel<0, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+        if (vol) dual_step_kernel<0, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
+        else if (live) dual_step_kernel<0, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
+        else dual_step_kernel<0, false, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
     }
     return cudaGetLastError();
 }
@@ -411,9 +415,11 @@ cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStre
 {
     const int nb = (step_blocks(P) + 1) / 2;
     if (P.D > 1)
-        primal_step_kernel<true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz);
+        primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz);
+    else if (P.live != nullptr)
+        primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
     else
-        primal_step_kernel<false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
+        primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
     return cudaGetLastError();
 }
 
