@@ -110,8 +110,10 @@ adj_primal_local_kernel(const LiftParams P, const float2 *__restrict__ x_n,
 }
 
 // ---------------------------------------------------------------------------
+// Four blocks per SM (64 registers, a few bytes spilled): the dual-number
+// projection below otherwise holds 80 registers and leaves three.
 template <int KIND>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, 4)
 adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
                       const float4 *__restrict__ y_n, const float2 *__restrict__ G,
                       float4 *__restrict__ ay, float *__restrict__ aq,
@@ -221,7 +223,9 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
             gf[pix] += s2.total.y;
         }
     }
-    // per-block sums of the scalar gradients (fixed order)
+    // per-block sums of the scalar gradients (fixed order), added to the
+    // block's own slot: each slot accumulates over the reverse iterations in
+    // their order, and one fixed-order pass sums the slots at the end
     for (int off = 16; off > 0; off >>= 1) {
         gl += __shfl_down_sync(0xffffffffu, gl, off);
         ga += __shfl_down_sync(0xffffffffu, ga, off);
@@ -233,9 +237,9 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
     if (tid == 0) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int j = 0; j < kAdjThreads / 32; ++j) { a0 += red[0][j]; a1 += red[1][j]; a2 += red[2][j]; }
-        partial[3 * blockIdx.x + 0] = a0;
-        partial[3 * blockIdx.x + 1] = a1;
-        partial[3 * blockIdx.x + 2] = a2;
+        partial[3 * blockIdx.x + 0] += a0;
+        partial[3 * blockIdx.x + 1] += a1;
+        partial[3 * blockIdx.x + 2] += a2;
     }
 }
 
@@ -255,7 +259,7 @@ adj_dual_gather_kernel(const LiftParams P, const float2 *__restrict__ A, float2 
     axb[o].x += add;
 }
 
-// Accumulate the per-block scalar partials into acc[3] in a fixed order.
+// Sum the per-block scalar partials into acc[3] in a fixed order.
 __global__ void adj_finish_kernel(const double *__restrict__ partial, int nblocks,
                                   double *__restrict__ acc)
 {
@@ -275,7 +279,7 @@ __global__ void adj_finish_kernel(const double *__restrict__ partial, int nblock
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         for (int j = 0; j < static_cast<int>(blockDim.x / 32); ++j) { s0 += red[0][j]; s1 += red[1][j]; s2 += red[2][j]; }
-        acc[0] += s0; acc[1] += s1; acc[2] += s2;
+        acc[0] = s0; acc[1] = s1; acc[2] = s2;
     }
 }
 
@@ -314,9 +318,12 @@ cudaError_t launch_adj_iteration(const LiftParams &P, const LiftState &Sn, const
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     adj_dual_gather_kernel<<<nb, kAdjThreads, 0, st>>>(P, Aj.A, Aj.axb);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    adj_finish_kernel<<<1, 256, 0, st>>>(Aj.partial, nb, Aj.acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_finish(const LiftParams &P, const AdjState &Aj, cudaStream_t st)
+{
+    adj_finish_kernel<<<1, 256, 0, st>>>(Aj.partial, adjoint_blocks(P), Aj.acc);
     return cudaGetLastError();
 }
 

@@ -1231,6 +1231,8 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f, do
     LIFT_CK(cudaMemsetAsync(A.aq, 0, N * sizeof(float), h->stream));
     LIFT_CK(cudaMemsetAsync(A.gf, 0, N * sizeof(float), h->stream));
     LIFT_CK(cudaMemsetAsync(A.acc, 0, 3 * sizeof(double), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.partial, 0, 3 * sizeof(double) * lift::adjoint_blocks(h->P),
+                            h->stream));
     const int nck = (h->unrolled_iters + C - 1) / C;
     for (int c = nck - 1; c >= 0; --c) {
         const int len = std::min(C, h->unrolled_iters - c * C);
@@ -1245,6 +1247,7 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f, do
             LIFT_CK(lift::launch_adj_iteration(h->P, state_at(h, h->seg + sb * j),
                                                state_at(h, h->seg + sb * (j + 1)), A, h->stream));
     }
+    LIFT_CK(lift::launch_adj_finish(h->P, A, h->stream));
     if (grad_f)
         LIFT_CK(cudaMemcpyAsync(grad_f, A.gf, N * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (grad_scalars) {

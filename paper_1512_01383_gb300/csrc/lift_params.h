@@ -82,6 +82,7 @@ int adjoint_blocks(const LiftParams &P);
 cudaError_t launch_adj_seed(const LiftParams &P, const float *grad_u, float2 *ax, cudaStream_t st);
 cudaError_t launch_adj_iteration(const LiftParams &P, const LiftState &Sn, const LiftState &Sn1,
                                  const AdjState &A, cudaStream_t st);
+cudaError_t launch_adj_finish(const LiftParams &P, const AdjState &Aj, cudaStream_t st);
 
 // setup_reduce.cu
 cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);
