@@ -672,8 +672,10 @@ struct lift_batch_ctx {
     std::vector<int> ntiles;            // per instance, for the current tile width
     void *arena = nullptr;              // all per-instance device arrays
     lift::InstDesc *desc = nullptr;     // device [n]
-    int *tile_inst = nullptr;           // device [total tiles]
-    int total_tiles = 0;
+    int *tile_inst = nullptr;           // device [total tiles]: instance of each tile
+    int *pair_inst = nullptr;           // device [total pairs]: dual step in tile pairs
+    int *single_inst = nullptr;         // device [total singles]: dual step in single tiles
+    int total_tiles = 0, total_pairs = 0, total_singles = 0;
     int *live = nullptr;                // device [n]: 1 = still iterating
     std::vector<int> live_h;
     std::vector<long long> iters_h;     // iterations done per instance
@@ -699,7 +701,8 @@ void free_batch(lift_batch b)
 {
     if (!b) return;
     drop_graph(b);
-    void *ptrs[] = {b->arena, b->desc, b->tile_inst, b->live, b->partial, b->dout, b->ubuf};
+    void *ptrs[] = {b->arena, b->desc, b->tile_inst, b->pair_inst, b->single_inst, b->live,
+                    b->partial, b->dout, b->ubuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->hout) cudaFreeHost(b->hout);
@@ -713,7 +716,7 @@ void free_batch(lift_batch b)
 int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 {
     std::vector<lift::InstDesc> d(b->n);
-    std::vector<int> ti;
+    std::vector<int> ti, pi, si;
     int t0 = 0;
     b->big.clear();
     b->Pbig.clear();
@@ -730,27 +733,43 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
             b->big.push_back(j);
             b->Pbig.push_back(Ps);
             b->ntiles[j] = 0;
-            d[j].tile0 = 0;
-            d[j].ntiles = 0;
+            d[j].tile0 = d[j].ntiles = d[j].pair0 = d[j].npairs = 0;
             continue;
         }
         b->ntiles[j] = nt;
         d[j].tile0 = t0;
         d[j].ntiles = nt;
+        std::vector<int> &ul = b->P[j].k >= lift::kPairMinK ? pi : si;
+        d[j].pair0 = static_cast<int>(ul.size());
+        d[j].npairs = b->P[j].k >= lift::kPairMinK ? (nt + 1) / 2 : nt;
         ti.insert(ti.end(), nt, j);
+        ul.insert(ul.end(), d[j].npairs, j);
         t0 += nt;
     }
-    if (ti.empty()) ti.push_back(0);    // keep a valid allocation; total_tiles stays 0
+    const int np = static_cast<int>(pi.size()), ns = static_cast<int>(si.size());
+    if (ti.empty()) ti.push_back(0);    // keep valid allocations; the totals stay 0
+    if (pi.empty()) pi.push_back(0);
+    if (si.empty()) si.push_back(0);
     if (b->tile_inst) cudaFree(b->tile_inst);
-    b->tile_inst = nullptr;
+    if (b->pair_inst) cudaFree(b->pair_inst);
+    if (b->single_inst) cudaFree(b->single_inst);
+    b->tile_inst = b->pair_inst = b->single_inst = nullptr;
     int rc = dev_alloc(reinterpret_cast<void **>(&b->tile_inst), ti.size() * sizeof(int));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->pair_inst), pi.size() * sizeof(int));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->single_inst), si.size() * sizeof(int));
     if (rc != LIFT_OK) return rc;
     LIFT_CK(cudaMemcpyAsync(b->tile_inst, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b->stream));
+    LIFT_CK(cudaMemcpyAsync(b->pair_inst, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream));
+    LIFT_CK(cudaMemcpyAsync(b->single_inst, si.data(), si.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream));
     LIFT_CK(cudaMemcpyAsync(b->desc, d.data(), d.size() * sizeof(lift::InstDesc),
                             cudaMemcpyHostToDevice, b->stream));
     LIFT_CK(cudaStreamSynchronize(b->stream));   // host vectors die here
     b->total_tiles = t0;
+    b->total_pairs = np;
+    b->total_singles = ns;
     b->threads = threads;
     b->big_tiles = big_tiles;
     drop_graph(b);
@@ -760,8 +779,9 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 int batch_launch(lift_batch b, int iters)
 {
     for (int it = 0; it < iters; ++it) {
-        LIFT_CK(lift::launch_batch_iteration(b->kind, b->threads, b->desc, b->tile_inst, b->live,
-                                             b->total_tiles, b->stream));
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->pair_inst,
+                                             b->single_inst, b->live, b->total_tiles,
+                                             b->total_pairs, b->total_singles, b->stream));
         for (size_t m = 0; m < b->big.size(); ++m) {
             const LiftState &S = b->S[b->big[m]];
             LIFT_CK(lift::launch_dual_step(b->Pbig[m], S, b->stream));

@@ -218,14 +218,13 @@ __device__ __forceinline__ float pl_envelope(const float *__restrict__ t,
     return (1.0f - a) * rh[j] + a * rh[j + 1];
 }
 
-// Projection onto epi(max_j t_j y - rh_j): same monotone-derivative test as
-// the quadratic piece, walking the kinks from left to right.
-__device__ __forceinline__ void pl_project(const float *__restrict__ t,
-                                           const float *__restrict__ rh, int n,
-                                           float y0, float h0, float &yo, float &ho)
+// Projection of a point below the graph onto epi(max_j t_j y - rh_j): same
+// monotone-derivative test as the quadratic piece, walking the kinks from
+// left to right.
+__device__ __forceinline__ void pl_project_below(const float *__restrict__ t,
+                                                 const float *__restrict__ rh, int n,
+                                                 float y0, float h0, float &yo, float &ho)
 {
-    const float phi0 = pl_conj(t, rh, n, y0);
-    if (h0 >= phi0) { yo = y0; ho = h0; return; }
     float tj = t[0], rj = rh[0];
     for (int j = 0; j < n - 1; ++j) {
         const float tn = t[j + 1], rn = rh[j + 1];
@@ -241,6 +240,14 @@ __device__ __forceinline__ void pl_project(const float *__restrict__ t,
     }
     const float y = (y0 + tj * (h0 + rj)) / (1.0f + tj * tj);
     yo = y; ho = tj * y - rj;
+}
+
+__device__ __forceinline__ void pl_project(const float *__restrict__ t,
+                                           const float *__restrict__ rh, int n,
+                                           float y0, float h0, float &yo, float &ho)
+{
+    if (h0 >= pl_conj(t, rh, n, y0)) { yo = y0; ho = h0; return; }
+    pl_project_below(t, rh, n, y0, h0, yo, ho);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,21 +301,35 @@ __device__ __forceinline__ float quad_conj_direct(const LiftParams &P, float f, 
 }
 
 template <int KIND>
-__device__ __forceinline__ void piece_project(const LiftParams &P, int pix, int i, float l,
-                                              float y0, float h0, float &yo, float &ho)
+__device__ __forceinline__ bool piece_in_epigraph(const LiftParams &P, int pix, int i, float l,
+                                                  float y0, float h0)
 {
     if (KIND == 2) {
         const int b0 = __ldg(P.bstart + i), n = __ldg(P.bstart + i + 1) - b0 + 1;
-        pl_project(P.bpos + b0, P.rhat + (size_t)pix * P.nb + b0, n, y0, h0, yo, ho);
-        return;
+        return h0 >= pl_conj(P.bpos + b0, P.rhat + (size_t)pix * P.nb + b0, n, y0);
     }
-    if (h0 >= quad_conj_direct(P, __ldg(P.f + pix), l, l + P.delta, y0)) {
-        yo = y0;
-        ho = h0;
+    return h0 >= quad_conj_direct(P, __ldg(P.f + pix), l, l + P.delta, y0);
+}
+
+template <int KIND>
+__device__ __forceinline__ void piece_project_below(const LiftParams &P, int pix, int i, float l,
+                                                    float y0, float h0, float &yo, float &ho)
+{
+    if (KIND == 2) {
+        const int b0 = __ldg(P.bstart + i), n = __ldg(P.bstart + i + 1) - b0 + 1;
+        pl_project_below(P.bpos + b0, P.rhat + (size_t)pix * P.nb + b0, n, y0, h0, yo, ho);
         return;
     }
     const QPiece q = make_qpiece(P, pix, l, l + P.delta);
     qpiece_project(q, y0, h0, yo, ho);
+}
+
+template <int KIND>
+__device__ __forceinline__ void piece_project(const LiftParams &P, int pix, int i, float l,
+                                              float y0, float h0, float &yo, float &ho)
+{
+    if (piece_in_epigraph<KIND>(P, pix, i, l, y0, h0)) { yo = y0; ho = h0; return; }
+    piece_project_below<KIND>(P, pix, i, l, y0, h0, yo, ho);
 }
 
 template <int KIND>

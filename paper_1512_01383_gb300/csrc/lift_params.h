@@ -54,7 +54,9 @@ struct LiftState {
 struct InstDesc {
     LiftParams P;
     LiftState S;
-    int tile0, ntiles;
+    int tile0, ntiles;      // its tiles in the batch's tile list (primal step)
+    int pair0, npairs;      // its units in its dual list: the tile pairs (k >= kPairMinK)
+                            // or the single tiles of the dual step
 };
 
 // Adjoint buffers of the differentiable solve (adjoint.cu).
@@ -69,13 +71,17 @@ struct AdjState {
 };
 
 constexpr int kStepThreads = 256;
+// The dual step of quadratic pieces on an image takes two tiles per block,
+// with packed projections, from this many intervals per pixel on.
+constexpr int kPairMinK = 4;
 
 // pdhg_step.cu
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
 
-cudaError_t launch_batch_iteration(int kind, int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *live, int ntiles, cudaStream_t st);
+cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
+                                   const int *pair_inst, const int *single_inst, const int *live,
+                                   int ntiles, int npairs, int nsingle, cudaStream_t st);
 
 // adjoint.cu
 int adjoint_blocks(const LiftParams &P);

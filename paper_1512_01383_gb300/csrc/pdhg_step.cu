@@ -211,6 +211,118 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
     y[o] = make_float4(v, z, px, py);
 }
 
+// Two consecutive tiles (2 pair, 2 pair + 1) of a quadratic-type problem in
+// one block, each thread owning one record of each.  The epigraph projection
+// is the only divergent part of the step: after the first iterations only a
+// few records per warp leave the epigraph (about 2 of 32 per tile on the
+// 512^2, L = 20 denoising problem, yet nearly every warp holds some).  The
+// records below the graph of both tiles are packed into one pass of the warp
+// through a per-warp queue in shared memory (no block barrier), so a warp runs
+// the projection once for two tiles instead of once per tile.  Each record's
+// arithmetic is that of dual_tile.
+template <int THREADS>
+struct PairSmem {
+    float2 in[THREADS];
+    float2 last[THREADS / 32];
+    float4 queue[THREADS / 32][64];
+};
+
+template <int THREADS, bool VOL>
+__device__ __forceinline__ void dual_pair(const LiftParams &P, const float2 *__restrict__ xbar,
+                                          float4 *__restrict__ y, float *__restrict__ q,
+                                          float *__restrict__ pz, int pair, PairSmem<THREADS> &sm)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int lp, i;
+    split_thread(P, tid, lp, i);
+    int pix[2]; bool act[2]; size_t o[2]; float2 xb[2]; float4 d[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        pix[u] = (2 * pair + u) * P.ppb + lp;
+        act[u] = lp < P.ppb && pix[u] < P.N;
+        o[u] = static_cast<size_t>(pix[u]) * P.k + i;
+        xb[u] = make_float2(0.f, 0.f);
+        d[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act[u]) { xb[u] = xbar[o[u]]; d[u] = y[o[u]]; }
+    }
+    const SegScan2 sc = block_segmented_scan2(make_float2(xb[0].y, xb[1].y), lp * P.k, P.k, tid,
+                                              act[0], sm.in, sm.last);
+    const float4 ic = __ldg(P.icst + (lp < P.ppb ? i : 0));  // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+    float px[2], py[2], y0[2], h0[2];
+    bool below[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        px[u] = py[u] = y0[u] = h0[u] = 0.0f;
+        below[u] = false;
+        if (!act[u]) continue;
+        const int row = pixel_row(P, pix[u]);
+        const int col = pix[u] - row * P.W;
+        const int yy = VOL ? row_in_slice(P, row) : row;
+
+        // TV dual: forward differences (Neumann), ascent, ball (or box) projection
+        const float gx = col + 1 < P.W ? xbar[o[u] + P.k].x - xb[u].x : 0.0f;
+        const float gy = yy + 1 < P.H ? xbar[o[u] + static_cast<size_t>(P.W) * P.k].x - xb[u].x
+                                      : 0.0f;
+        px[u] = d[u].z + P.sigma_p * gx;
+        py[u] = d[u].w + P.sigma_p * gy;
+        float pzv = 0.0f;
+        if (VOL) {
+            const float gz = pix[u] < P.N - P.HW
+                                 ? xbar[o[u] + static_cast<size_t>(P.HW) * P.k].x - xb[u].x : 0.0f;
+            pzv = pz[o[u]] + P.sigma_p * gz;
+        }
+        if (P.aniso) {
+            px[u] = fminf(fmaxf(px[u], -ic.w), ic.w);
+            py[u] = fminf(fmaxf(py[u], -ic.w), ic.w);
+            if (VOL) pzv = fminf(fmaxf(pzv, -ic.w), ic.w);
+        } else {
+            const float n2 = px[u] * px[u] + py[u] * py[u] + (VOL ? pzv * pzv : 0.0f);
+            if (n2 > ic.w * ic.w) {
+                const float sc2 = ic.w * rsqrtf(n2);
+                px[u] *= sc2;
+                py[u] *= sc2;
+                if (VOL) pzv *= sc2;
+            }
+        }
+        if (VOL) pz[o[u]] = pzv;
+
+        // data duals: sum of sbar over the pixel's later intervals = total - inclusive
+        const float total = u == 0 ? sc.total.x : sc.total.y;
+        const float tail = total - (u == 0 ? sc.incl.x : sc.incl.y);
+        const float v = d[u].x + ic.z * (xb[u].x + P.delta * tail - ic.x * xb[u].y);
+        const float z = d[u].y + ic.z * xb[u].y;
+        if (i == 0) q[pix[u]] -= P.sigma_q * (1.0f + P.delta * total);
+        y0[u] = v * P.inv_delta;
+        h0[u] = z * P.inv_delta;
+        below[u] = !piece_in_epigraph<0>(P, pix[u], i, ic.x, y0[u], h0[u]);
+    }
+
+    // queue slots: tile 0's records below the graph, then tile 1's (at most 64)
+    const unsigned m0 = __ballot_sync(0xffffffffu, below[0]);
+    const unsigned m1 = __ballot_sync(0xffffffffu, below[1]);
+    const int n0 = __popc(m0), n = n0 + __popc(m1);
+    const unsigned lt = (1u << lane) - 1u;
+    const int e0 = __popc(m0 & lt), e1 = n0 + __popc(m1 & lt);
+    float4 *qw = sm.queue[warp];
+    if (below[0]) qw[e0] = make_float4(y0[0], h0[0], __int_as_float(pix[0]), __int_as_float(i));
+    if (below[1]) qw[e1] = make_float4(y0[1], h0[1], __int_as_float(pix[1]), __int_as_float(i));
+    __syncwarp();
+    // (v, z) onto Delta * epi(rho_i^*), packed
+    for (int j = lane; j < n; j += 32) {
+        const float4 e = qw[j];
+        const int qp = __float_as_int(e.z), qi = __float_as_int(e.w);
+        float yo, ho;
+        piece_project_below<0>(P, qp, qi, __ldg(P.icst + qi).x, e.x, e.y, yo, ho);
+        qw[j] = make_float4(yo, ho, e.z, e.w);
+    }
+    __syncwarp();
+    if (below[0]) { const float4 r = qw[e0]; y0[0] = r.x; h0[0] = r.y; }
+    if (below[1]) { const float4 r = qw[e1]; y0[1] = r.x; h0[1] = r.y; }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (act[u]) y[o[u]] = make_float4(P.delta * y0[u], P.delta * h0[u], px[u], py[u]);
+}
+
 template <int THREADS>
 __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restrict__ x,
                                             float2 *__restrict__ xbar,
@@ -254,6 +366,9 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
 }
 
 // LIVE: a batch member, whose blocks return while its live flag is 0.
+// One tile per block: sampled costs (their projection walks the hull's kinks
+// and packing costs more registers than it saves), volumes, and quadratic
+// pieces with k < kPairMinK (few records per pixel, little to pack).
 template <int KIND, bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
@@ -263,6 +378,18 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     __shared__ float s_last[kStepThreads / 32];
     if (LIVE && *P.live == 0) return;
     dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x, s_in, s_last, pz);
+}
+
+// Quadratic pieces on an image with k >= kPairMinK: two tiles per block with
+// the projections packed (dual_pair).
+template <bool LIVE>
+__global__ void __launch_bounds__(kStepThreads)
+dual_pair_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
+                 float *__restrict__ q)
+{
+    __shared__ PairSmem<kStepThreads> sm;
+    if (LIVE && *P.live == 0) return;
+    dual_pair<kStepThreads, false>(P, xbar, y, q, nullptr, blockIdx.x, sm);
 }
 
 // Single-instance primal step: each block takes two consecutive tiles and
@@ -334,18 +461,37 @@ __device__ __forceinline__ void stage_desc(const InstDesc *__restrict__ D, int i
     __syncthreads();
 }
 
-template <int KIND, int THREADS>
+// Batches hold quadratic-type images only.  Instances with k >= kPairMinK
+// take their dual step in tile pairs, the others in single tiles, as their
+// single-instance kernels do; the two kinds of unit have a list and a kernel
+// each (one kernel holding both bodies would compile them differently from
+// the single-instance kernels).  Block b takes unit b - pair0 of instance
+// unit_inst[b].
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+batch_dual_pair_kernel(const InstDesc *__restrict__ D, const int *__restrict__ unit_inst,
+                       const int *__restrict__ live)
+{
+    __shared__ PairSmem<THREADS> sm;
+    __shared__ InstDesc sd;
+    const int inst = unit_inst[blockIdx.x];
+    if (!live[inst]) return;
+    stage_desc(D, inst, &sd);
+    dual_pair<THREADS, false>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, nullptr, blockIdx.x - sd.pair0, sm);
+}
+
+template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS)
-batch_dual_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile_inst,
-                  const int *__restrict__ live)
+batch_dual_tile_kernel(const InstDesc *__restrict__ D, const int *__restrict__ unit_inst,
+                       const int *__restrict__ live)
 {
     __shared__ float s_in[THREADS];
     __shared__ float s_last[THREADS / 32];
     __shared__ InstDesc sd;
-    const int inst = tile_inst[blockIdx.x];
+    const int inst = unit_inst[blockIdx.x];
     if (!live[inst]) return;
     stage_desc(D, inst, &sd);
-    dual_tile<KIND, THREADS>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, blockIdx.x - sd.tile0, s_in, s_last);
+    dual_tile<0, THREADS>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, blockIdx.x - sd.pair0, s_in, s_last);
 }
 
 template <int THREADS>
@@ -364,27 +510,30 @@ batch_primal_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile
 }
 
 template <int THREADS>
-static cudaError_t launch_batch_t(int kind, const InstDesc *D, const int *tile_inst,
-                                  const int *live, int ntiles, cudaStream_t st)
+static cudaError_t launch_batch_t(const InstDesc *D, const int *tile_inst, const int *pair_inst,
+                                  const int *single_inst, const int *live, int ntiles, int npairs,
+                                  int nsingle, cudaStream_t st)
 {
-    if (kind == 2)
-        batch_dual_kernel<2, THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
-    else
-        batch_dual_kernel<0, THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
+    if (npairs > 0) batch_dual_pair_kernel<THREADS><<<npairs, THREADS, 0, st>>>(D, pair_inst, live);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (nsingle > 0)
+        batch_dual_tile_kernel<THREADS><<<nsingle, THREADS, 0, st>>>(D, single_inst, live);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batch_primal_kernel<THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_iteration(int kind, int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *live, int ntiles, cudaStream_t st)
+cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
+                                   const int *pair_inst, const int *single_inst, const int *live,
+                                   int ntiles, int npairs, int nsingle, cudaStream_t st)
 {
     if (ntiles <= 0) return cudaSuccess;
     switch (threads) {
-    case 128: return launch_batch_t<128>(kind, D, tile_inst, live, ntiles, st);
-    case 256: return launch_batch_t<256>(kind, D, tile_inst, live, ntiles, st);
-    case 512: return launch_batch_t<512>(kind, D, tile_inst, live, ntiles, st);
+    case 128: return launch_batch_t<128>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
+    case 256: return launch_batch_t<256>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
+    case 512: return launch_batch_t<512>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -397,8 +546,13 @@ static inline int step_blocks(const LiftParams &P)
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
 {
     // volumes never belong to a batch, so VOL and LIVE do not meet
-    const int nb = step_blocks(P);
+    const int nb = step_blocks(P), npair = (nb + 1) / 2;
     const bool vol = P.D > 1, live = P.live != nullptr;
+    if (P.kind != 2 && !vol && P.k >= kPairMinK) {
+        if (live) dual_pair_kernel<true><<<npair, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+        else dual_pair_kernel<false><<<npair, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+        return cudaGetLastError();
+    }
     if (P.kind == 2) {
         if (vol) dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
         else if (live) dual_step_kernel<2, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
