@@ -142,6 +142,20 @@ int lift_reset(lift_handle h);
  * enqueueing. */
 int lift_iterate(lift_handle h, int iters);
 
+/* lift_set_resident: small image problems (whole 256-thread tiles, at most 8
+ * per CTA on a cluster of at most 16 CTAs, their state within 200 KB of
+ * shared memory per CTA: e.g. 64 x 64 pixels with L up to 20) run each call
+ * of lift_iterate as one launch of a thread-block cluster that keeps the
+ * state in shared memory for all the iterations and reads neighbouring
+ * CTAs' halo values through distributed shared memory; the launches and the
+ * round trips to L2 between half-steps go away.  The map is the iteration of
+ * Sec. 4 as for every other problem (same records, same arithmetic).  This
+ * is on by default where the problem fits; enable = 0 makes lift_iterate use
+ * the per-half-step kernels (graph replay) instead.  *active (may be NULL)
+ * tells whether lift_iterate now takes the resident path.  Volumes never do.
+ * lift_dual_step / lift_primal_step always use the per-half-step kernels. */
+int lift_set_resident(lift_handle h, int enable, int *active);
+
 /* lift_dual_step / lift_primal_step: one half-step each, the two kernels
  * that lift_iterate runs per iteration (dual first, then primal).  Exposed
  * so that callers can time or interleave them.  Asynchronous. */

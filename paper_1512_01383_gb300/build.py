@@ -15,15 +15,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblift_gb300.so")
-SOURCES = ["pdhg_step.cu", "setup_reduce.cu", "lift_api.cu", "adjoint.cu"]
+SOURCES = ["pdhg_step.cu", "setup_reduce.cu", "lift_api.cu", "adjoint.cu", "resident.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
-# The half-step kernels use approximate division / square root (within a few
-# ulp, far inside the FP32-vs-FP64 parity tolerance), and so does the adjoint,
-# which recomputes their intermediate values; the energy reductions and the
+# The half-step kernels (and their cluster-resident form) use approximate
+# division / square root (within a few ulp, far inside the FP32-vs-FP64
+# parity tolerance), and so does the adjoint, which recomputes their
+# intermediate values; the energy reductions and the
 # setup keep IEEE arithmetic.
-EXTRA = {"pdhg_step.cu": ["-use_fast_math"], "adjoint.cu": ["-use_fast_math"]}
+EXTRA = {"pdhg_step.cu": ["-use_fast_math"], "adjoint.cu": ["-use_fast_math"],
+         "resident.cu": ["-use_fast_math"]}
 
 
 def _compile(src: str) -> tuple[str, str]:

@@ -51,6 +51,9 @@ struct lift_ctx {
     int adaptive = 0;
     char *prev = nullptr;               // state at the previous check
     bool prev_valid = false;
+    // small problems: whole calls of lift_iterate inside one cluster
+    lift::ResidentPlan resident{};
+    bool resident_on = true;            // caller's preference (lift_set_resident)
 };
 
 namespace {
@@ -391,6 +394,7 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     if (rc != LIFT_OK) { free_ctx(h); return rc; }
     rc = lift_reset(h);
     if (rc != LIFT_OK) { free_ctx(h); return rc; }
+    lift::plan_resident(h->P, h->resident);
     // host-side vectors die with this scope: finish the uploads first
     CUDA_OR_FAIL(cudaStreamSynchronize(h->stream));
 #undef CUDA_OR_FAIL
@@ -475,6 +479,10 @@ static int ensure_iter_graph(lift_handle h)
 int lift_iterate(lift_handle h, int iters)
 {
     if (!h || iters < 0) return LIFT_ERR_ARG;
+    if (iters > 0 && h->resident.ok && h->resident_on) {
+        LIFT_CK(lift::launch_resident(h->P, h->S, iters, h->resident, h->stream));
+        return LIFT_OK;
+    }
     const int reps = iters / h->check_every;
     if (reps > 0) {
         int rc = ensure_iter_graph(h);
@@ -556,6 +564,14 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
         }
     }
     return LIFT_ERR_NOT_CONVERGED;
+}
+
+int lift_set_resident(lift_handle h, int enable, int *active)
+{
+    if (!h) return LIFT_ERR_ARG;
+    h->resident_on = enable != 0;
+    if (active) *active = h->resident.ok && h->resident_on ? 1 : 0;
+    return LIFT_OK;
 }
 
 int lift_get_balance(lift_handle h, double *theta)

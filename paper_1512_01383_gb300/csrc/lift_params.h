@@ -90,6 +90,18 @@ cudaError_t launch_adj_iteration(const LiftParams &P, const LiftState &Sn, const
                                  const AdjState &A, cudaStream_t st);
 cudaError_t launch_adj_finish(const LiftParams &P, const AdjState &Aj, cudaStream_t st);
 
+// resident.cu: whole check intervals of a small image problem inside one
+// thread-block cluster, the state in shared memory.
+struct ResidentPlan {
+    bool ok = false;
+    int ctas = 0;      // CTAs of the cluster (one cluster)
+    int ppc = 0;       // pixels per CTA (whole tiles)
+    size_t smem = 0;   // dynamic shared memory per CTA
+};
+bool plan_resident(const LiftParams &P, ResidentPlan &R);
+cudaError_t launch_resident(const LiftParams &P, const LiftState &S, int iters,
+                            const ResidentPlan &R, cudaStream_t st);
+
 // setup_reduce.cu
 cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);
 // Writes per-block partial sums {P_hat, D, E_nc} to partial[nblocks] and the

@@ -31,7 +31,7 @@ EXPORTED = (
     "lift_batch_get_state", "lift_batch_autotune", "lift_batch_schedule",
     "lift_batch_set_schedule",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
-    "lift_get_balance",
+    "lift_get_balance", "lift_set_resident",
 )
 
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "lift_unrolled_forward": (C.c_int, [vp, C.c_int, C.c_int]),
         "lift_unrolled_backward": (C.c_int, [vp, vp, vp, dp]),
         "lift_get_balance": (C.c_int, [vp, dp]),
+        "lift_set_resident": (C.c_int, [vp, C.c_int, ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -191,6 +192,15 @@ def lift_get_balance(h: int) -> float:
     return t.value
 
 
+def lift_set_resident(h: int, enable: bool) -> bool:
+    """Prefer (or not) the cluster-resident iteration for small problems;
+    returns whether lift_iterate now takes it."""
+    a = C.c_int()
+    _check(load().lift_set_resident(C.c_void_p(h), 1 if enable else 0, C.byref(a)),
+           "lift_set_resident")
+    return bool(a.value)
+
+
 def lift_energy(h: int) -> tuple[float, float, float]:
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     _check(load().lift_energy(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)), "lift_energy")
@@ -274,7 +284,7 @@ class Solver:
                  nu: float = 0.0, f=None, cost=None, sample_min: float = 0.0,
                  sample_max: float = 1.0, check_every: int = 100, stream: int | None = None,
                  step_balance: float = 1.0, adaptive_balance: bool = False,
-                 anisotropic: bool = False, depth: int = 1):
+                 anisotropic: bool = False, depth: int = 1, resident: bool = True):
         self.kind, self.H, self.W, self.L, self.k = kind, H, W, L, L - 1
         self.D = max(int(depth), 1)
         self.spec = make_spec(kind, H, W, L, gamma_min, gamma_max, lam, alpha, nu, f, cost,
@@ -283,6 +293,8 @@ class Solver:
         self._keep = (f, cost)
         self.h = lift_create(self.spec, stream)
         self._keep = None
+        if not resident:
+            lift_set_resident(self.h, False)
 
     def close(self):
         if getattr(self, "h", None):

@@ -47,7 +47,7 @@ def test_batch_equals_single_handles_bitwise(big_tiles, n_big):
         G.lift_batch_iterate(b, 130)          # two graph replays + 30 direct iterations
         e = G.lift_batch_energy(b)
         for j, c in enumerate(cases):
-            with gpu_solver(c) as s:
+            with gpu_solver(c, resident=False) as s:
                 s.iterate(130)
                 ut = s.unlift()
                 Pg, Dg, Eg = s.energy()

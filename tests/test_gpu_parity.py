@@ -121,12 +121,18 @@ def test_balanced_steps_match_oracle(kind, H, W, L, iters, theta):
         assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
 
 
+@pytest.mark.parametrize("resident", [True, False])
 @pytest.mark.parametrize("kind,H,W,L,iters", PARITY_CASES)
-def test_iterations_match_oracle(kind, H, W, L, iters):
+def test_iterations_match_oracle(kind, H, W, L, iters, resident):
+    """Both ways lift_iterate runs small problems: inside one thread-block
+    cluster (the default where the problem fits) and as per-half-step
+    kernels."""
     _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
     c = case(kind, H, W, L, 300 + H + L)
     P, X = oracle_run(c, iters)
-    with gpu_solver(c) as s:
+    with gpu_solver(c, resident=resident) as s:
+        assert G.lift_set_resident(s.h, resident) == resident
         s.iterate(iters)
         ut = s.unlift()
         st = s.state()
@@ -300,7 +306,8 @@ def test_graph_replay_equals_direct_launches():
     _require_gpu()
     from paper_1512_01383_gb300 import lift as G
     c = case(1, 23, 19, 6, 951)
-    with gpu_solver(c, check_every=40) as a, gpu_solver(c, check_every=40) as b:
+    with gpu_solver(c, check_every=40, resident=False) as a, \
+            gpu_solver(c, check_every=40, resident=False) as b:
         a.iterate(130)                     # 3 graph replays + 10 direct iterations
         for _ in range(130):
             G.lift_dual_step(b.h)
