@@ -219,9 +219,10 @@ def run_batch(G, torch, stream, dev, n=64, smin=128, smax=1024, iters=100, reps=
 
 
 def time_iters(G, torch, solver, iters, stream):
-    """Milliseconds for `iters` iterations of a solver on `stream` (events)."""
+    """Milliseconds for `iters` iterations of a solver on `stream` (events),
+    after the same number untimed, which also builds the iteration graph."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    solver.iterate(3)
+    solver.iterate(iters)
     torch.cuda.synchronize()
     e0.record(stream)
     solver.iterate(iters)

@@ -142,6 +142,22 @@ int lift_reset(lift_handle h);
  * enqueueing. */
 int lift_iterate(lift_handle h, int iters);
 
+/* lift_set_bands: the graph that lift_iterate replays for each check
+ * interval splits the image (volume) into row (slice) bands of whole tiles,
+ * each at least one row (slice) long, and orders each band's half-steps only
+ * after those of its own and its adjacent bands that it depends on: the dual
+ * step of band j after the primal steps of bands j and j+1, the primal step
+ * of band j after the dual steps of bands j and j-1.  Every half-step then
+ * reads exactly what it reads in the one-stream order (the iterate is
+ * bitwise the same), while the issue-bound dual steps of some bands overlap
+ * the memory-bound primal steps of others.  bands = 0 chooses automatically
+ * (4 bands from 4096 tiles of 256 threads on, else 1), 1 turns banding off,
+ * 2..8 ask for that many (fewer when the bands would be too short).  *used
+ * (may be NULL) receives the number that lift_iterate will use.  The
+ * cluster-resident path (lift_set_resident) takes precedence where it
+ * applies. */
+int lift_set_bands(lift_handle h, int bands, int *used);
+
 /* lift_set_resident: small image problems (whole 256-thread tiles, at most 8
  * per CTA on a cluster of at most 16 CTAs, their state within 200 KB of
  * shared memory per CTA: e.g. 64 x 64 pixels with L up to 20) run each call

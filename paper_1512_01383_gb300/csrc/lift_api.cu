@@ -14,6 +14,8 @@
 using lift::LiftParams;
 using lift::LiftState;
 
+constexpr int kMaxBands = 8;
+
 struct lift_ctx {
     cudaStream_t stream = nullptr;
     int kind = 0;
@@ -22,6 +24,7 @@ struct lift_ctx {
     LiftParams P{};
     LiftState S{};
     float4 *icst = nullptr;
+    float4 *steps = nullptr;   // {tau_u, sigma_q, sigma_p, 0} (see LiftParams::steps)
     float *f = nullptr;        // quadratic kinds
     float *cost = nullptr;     // PL raw samples
     float *rhat = nullptr;     // PL convexified values
@@ -44,6 +47,11 @@ struct lift_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_iters = 0;
+    // banded graph: per band a stream for the dual and one for the primal
+    // half-steps, ordered by events (see ensure_iter_graph)
+    int bands_req = 0;                  // lift_set_bands: 0 = automatic
+    cudaStream_t band_s[2 * kMaxBands] = {};
+    cudaEvent_t band_e[2 * kMaxBands + 1] = {};
     // adaptive primal/dual balance (lift_solve)
     lift_spec spec_copy{};              // data pointers cleared; for re-deriving steps
     double theta = 1.0;
@@ -78,7 +86,7 @@ int dev_alloc(void **p, size_t bytes)
 void free_ctx(lift_ctx *h)
 {
     if (!h) return;
-    void *ptrs[] = {h->S.x, h->S.xbar, h->S.y, h->S.q, h->S.pz, h->icst, h->f, h->cost,
+    void *ptrs[] = {h->S.x, h->S.xbar, h->S.y, h->S.q, h->S.pz, h->icst, h->steps, h->f, h->cost,
                     h->rhat, h->bpos, h->bstart, h->ubuf, h->partial, h->dout};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -90,6 +98,10 @@ void free_ctx(lift_ctx *h)
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->gstream) cudaStreamDestroy(h->gstream);
+    for (cudaStream_t st : h->band_s)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : h->band_e)
+        if (ev) cudaEventDestroy(ev);
     if (h->prev) cudaFree(h->prev);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
@@ -225,6 +237,11 @@ int upload_data(lift_handle h, const float *data, int on_host)
 
 // Re-derive the step sizes for a new balance theta (icst and the scalar
 // steps; everything else of the parameters is unchanged).
+float4 step_scalars(const LiftParams &P)
+{
+    return make_float4(P.tau_u, P.sigma_q, P.sigma_p, 0.0f);
+}
+
 int set_theta(lift_handle h, double theta)
 {
     lift_spec sp = h->spec_copy;
@@ -239,11 +256,11 @@ int set_theta(lift_handle h, double theta)
     h->P.sigma_q = P2.sigma_q;
     h->P.sigma_p = P2.sigma_p;
     h->theta = theta;
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    if (h->graph) cudaGraphDestroy(h->graph);
-    h->gexec = nullptr;
-    h->graph = nullptr;
-    h->graph_iters = 0;
+    // the step kernels read icst and the scalar steps from device memory, so
+    // the captured iteration graph stays valid
+    const float4 st = step_scalars(h->P);
+    LIFT_CK(cudaMemcpyAsync(h->steps, &st, sizeof(float4), cudaMemcpyHostToDevice, h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));   // st dies here
     return LIFT_OK;
 }
 
@@ -356,6 +373,7 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     ALLOC(h->S.q, N * sizeof(float));
     if (P.D > 1) ALLOC(h->S.pz, Nk * sizeof(float));
     ALLOC(h->icst, k * sizeof(float4));
+    ALLOC(h->steps, sizeof(float4));
     ALLOC(h->ubuf, N * sizeof(float));
     ALLOC(h->partial, 3 * sizeof(double) * lift::energy_blocks(P));
     ALLOC(h->dout, 3 * sizeof(double));
@@ -381,6 +399,7 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     }
 #undef ALLOC
     P.icst = h->icst;
+    P.steps = h->steps;
     P.f = h->f;
     P.rhat = h->rhat;
     P.cost = h->cost;
@@ -389,6 +408,8 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
 
     CUDA_OR_FAIL(cudaMemcpyAsync(h->icst, ic.data(), k * sizeof(float4), cudaMemcpyHostToDevice,
                                  h->stream));
+    const float4 st0 = step_scalars(P);
+    CUDA_OR_FAIL(cudaMemcpyAsync(h->steps, &st0, sizeof(float4), cudaMemcpyHostToDevice, h->stream));
     const float *data = spec->kind == LIFT_PL_SAMPLED ? spec->cost : spec->f;
     rc = upload_data(h, data, spec->data_on_host);
     if (rc != LIFT_OK) { free_ctx(h); return rc; }
@@ -440,6 +461,21 @@ static void drop_iter_graph(lift_handle h)
     h->graph_iters = 0;
 }
 
+static int step_tiles(lift_handle h) { return (h->P.N + h->P.ppb - 1) / h->P.ppb; }
+
+// Number of bands of the iteration graph: 4 by default for problems of at
+// least 4096 tiles, fewer (down to 1) while a band would hold less than the
+// largest neighbour offset (a row of an image, a slice of a volume), so that
+// every halo value lies in the same or an adjacent band.
+static int bands_used(lift_handle h)
+{
+    int B = h->bands_req > 0 ? std::min(h->bands_req, kMaxBands) : (step_tiles(h) >= 4096 ? 4 : 1);
+    const long long span = h->P.D > 1 ? h->P.HW : h->P.W;
+    // boundaries fall on even tiles, so a band holds at least T/B - 2 tiles
+    while (B > 1 && (static_cast<long long>(step_tiles(h) / B - 2) * h->P.ppb <= span)) --B;
+    return B;
+}
+
 static int launch_iters(lift_handle h, cudaStream_t st, int iters)
 {
     for (int n = 0; n < iters; ++n) {
@@ -462,8 +498,59 @@ static int ensure_iter_graph(lift_handle h)
         LIFT_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         LIFT_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     }
+    const int B = bands_used(h);
+    if (B > 1 && !h->band_s[0]) {
+        for (int j = 0; j < 2 * kMaxBands; ++j)
+            LIFT_CK(cudaStreamCreateWithFlags(&h->band_s[j], cudaStreamNonBlocking));
+        for (int j = 0; j < 2 * kMaxBands + 1; ++j)
+            LIFT_CK(cudaEventCreateWithFlags(&h->band_e[j], cudaEventDisableTiming));
+    }
     LIFT_CK(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_iters(h, h->gstream, h->check_every);
+    int rc = LIFT_OK;
+    if (B == 1) {
+        rc = launch_iters(h, h->gstream, h->check_every);
+    } else {
+        // Rows of tiles in B bands (boundaries on even tiles, each at least a
+        // neighbour offset long).  Dual D(j, n) reads ubar of band j and of the
+        // first row of band j+1 and overwrites y of band j, which the primal
+        // step of band j+1 reads: it follows P(j, n-1) and P(j+1, n-1).  P(j,
+        // n) reads p of band j and of the last row of band j-1 and overwrites
+        // xbar of band j, which D(j-1, n) reads: it follows D(j, n) and D(j-1,
+        // n).  The graph keeps exactly these orders, so every half-step reads
+        // what it reads in the one-stream order (the same result, bitwise),
+        // while the issue-bound dual steps of some bands run beside the
+        // memory-bound primal steps of others.
+        const int T = step_tiles(h);
+        int b0[kMaxBands + 1];
+        for (int j = 0; j <= B; ++j)
+            b0[j] = j == B ? T : static_cast<int>(static_cast<long long>(T) * j / B) / 2 * 2;
+        cudaStream_t *sD = h->band_s, *sP = h->band_s + kMaxBands;
+        cudaEvent_t *eD = h->band_e, *eP = h->band_e + kMaxBands, fork = h->band_e[2 * kMaxBands];
+        cudaError_t e = cudaEventRecord(fork, h->gstream);
+        for (int j = 0; j < B && e == cudaSuccess; ++j) {
+            e = cudaStreamWaitEvent(sD[j], fork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sP[j], fork, 0);
+        }
+        for (int n = 0; n < h->check_every && e == cudaSuccess; ++n) {
+            for (int j = 0; j < B && e == cudaSuccess; ++j) {
+                if (n > 0) {
+                    e = cudaStreamWaitEvent(sD[j], eP[j], 0);
+                    if (e == cudaSuccess && j + 1 < B) e = cudaStreamWaitEvent(sD[j], eP[j + 1], 0);
+                }
+                if (e == cudaSuccess) e = lift::launch_dual_band(h->P, h->S, b0[j], b0[j + 1], sD[j]);
+                if (e == cudaSuccess) e = cudaEventRecord(eD[j], sD[j]);
+            }
+            for (int j = 0; j < B && e == cudaSuccess; ++j) {
+                e = cudaStreamWaitEvent(sP[j], eD[j], 0);
+                if (e == cudaSuccess && j > 0) e = cudaStreamWaitEvent(sP[j], eD[j - 1], 0);
+                if (e == cudaSuccess) e = lift::launch_primal_band(h->P, h->S, b0[j], b0[j + 1], sP[j]);
+                if (e == cudaSuccess) e = cudaEventRecord(eP[j], sP[j]);
+            }
+        }
+        // join every band's last primal step into the capture stream
+        for (int j = 0; j < B && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(h->gstream, eP[j], 0);
+        if (e != cudaSuccess) rc = LIFT_ERR_CUDA;
+    }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(h->gstream, &g);
     if (rc != LIFT_OK || e != cudaSuccess) {
@@ -564,6 +651,15 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
         }
     }
     return LIFT_ERR_NOT_CONVERGED;
+}
+
+int lift_set_bands(lift_handle h, int bands, int *used)
+{
+    if (!h || bands < 0) return LIFT_ERR_ARG;
+    h->bands_req = bands;
+    drop_iter_graph(h);
+    if (used) *used = bands_used(h);
+    return LIFT_OK;
 }
 
 int lift_set_resident(lift_handle h, int enable, int *active)
@@ -861,7 +957,8 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
 
     // one arena: per instance x, xbar, y, q, f, icst (256-byte aligned)
     std::vector<std::vector<float4>> ics(n);
-    std::vector<size_t> off(n * 6);
+    std::vector<size_t> off(n * 7);
+    std::vector<float4> st(n);
     size_t total = 0;
     auto take = [&](size_t bytes) { const size_t o = total; total += (bytes + 255) & ~size_t(255); return o; };
     int max_eblocks = 1;
@@ -869,12 +966,14 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
     for (int j = 0; j < n; ++j) {
         make_params(&specs[j], lift::kStepThreads, b->P[j], ics[j]);
         const size_t N = static_cast<size_t>(b->P[j].N), Nk = N * b->P[j].k;
-        off[6 * j + 0] = take(Nk * sizeof(float2));
-        off[6 * j + 1] = take(Nk * sizeof(float2));
-        off[6 * j + 2] = take(Nk * sizeof(float4));
-        off[6 * j + 3] = take(N * sizeof(float));
-        off[6 * j + 4] = take(N * sizeof(float));
-        off[6 * j + 5] = take(b->P[j].k * sizeof(float4));
+        off[7 * j + 0] = take(Nk * sizeof(float2));
+        off[7 * j + 1] = take(Nk * sizeof(float2));
+        off[7 * j + 2] = take(Nk * sizeof(float4));
+        off[7 * j + 3] = take(N * sizeof(float));
+        off[7 * j + 4] = take(N * sizeof(float));
+        off[7 * j + 5] = take(b->P[j].k * sizeof(float4));
+        off[7 * j + 6] = take(sizeof(float4));
+        st[j] = step_scalars(b->P[j]);
         max_eblocks = std::max(max_eblocks, lift::energy_blocks(b->P[j]));
         max_n = std::max(max_n, N);
     }
@@ -893,20 +992,23 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
     char *base = static_cast<char *>(b->arena);
     for (int j = 0; j < n; ++j) {
         LiftState &S = b->S[j];
-        S.x = reinterpret_cast<float2 *>(base + off[6 * j + 0]);
-        S.xbar = reinterpret_cast<float2 *>(base + off[6 * j + 1]);
-        S.y = reinterpret_cast<float4 *>(base + off[6 * j + 2]);
-        S.q = reinterpret_cast<float *>(base + off[6 * j + 3]);
-        float *f = reinterpret_cast<float *>(base + off[6 * j + 4]);
-        float4 *ic = reinterpret_cast<float4 *>(base + off[6 * j + 5]);
+        S.x = reinterpret_cast<float2 *>(base + off[7 * j + 0]);
+        S.xbar = reinterpret_cast<float2 *>(base + off[7 * j + 1]);
+        S.y = reinterpret_cast<float4 *>(base + off[7 * j + 2]);
+        S.q = reinterpret_cast<float *>(base + off[7 * j + 3]);
+        float *f = reinterpret_cast<float *>(base + off[7 * j + 4]);
+        float4 *ic = reinterpret_cast<float4 *>(base + off[7 * j + 5]);
         b->P[j].f = f;
         b->P[j].icst = ic;
+        b->P[j].steps = reinterpret_cast<float4 *>(base + off[7 * j + 6]);
         const size_t N = static_cast<size_t>(b->P[j].N);
         if (cudaMemcpyAsync(f, specs[j].f, N * sizeof(float),
                             specs[j].data_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             b->stream) != cudaSuccess ||
             cudaMemcpyAsync(ic, ics[j].data(), ics[j].size() * sizeof(float4),
-                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+                            cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(base + off[7 * j + 6], &st[j], sizeof(float4), cudaMemcpyHostToDevice,
+                            b->stream) != cudaSuccess) {
             free_batch(b);
             return LIFT_ERR_CUDA;
         }

@@ -29,6 +29,9 @@ struct LiftParams {
     float wtrunc;            // sqrt(nu/alpha): half-width of the parabola
     float tau_u, sigma_q, sigma_p;
     const float4 *icst;      // per interval {gamma_i, tau_s_i, sigma_vz_i, lambda*Delta}
+    const float4 *steps;     // {tau_u, sigma_q, sigma_p, 0} in device memory: the step
+                             // kernels read these (not the copies above), so a new
+                             // primal/dual balance needs no new iteration graph
     const float *f;          // [N] image (quadratic kinds)
     const float *rhat;       // [N][nb] convexified PL values at the breakpoints
     const float *cost;       // [N][ns] raw samples (PL)
@@ -36,6 +39,7 @@ struct LiftParams {
     const int *bstart;       // [k+1] first breakpoint of each interval (PL)
     int nb, ns;              // breakpoints, samples (PL)
     float smin, sh;          // sample j sits at smin + j*sh (PL)
+    int blk_off;             // first block of a band launch (0: the whole grid)
     const int *live;         // batch member run by the single-instance kernels:
                              // their blocks return while *live == 0 (null: run)
 };
@@ -77,6 +81,12 @@ constexpr int kPairMinK = 4;
 
 // pdhg_step.cu
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+// The half-steps on the tiles [t0, t1) only (t0 even): one band of a banded
+// iteration graph.
+cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, int t1,
+                             cudaStream_t st);
+cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
+                               cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
 
 cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,

@@ -105,17 +105,18 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
     const int col = pix - row * P.W;
     const int yy = VOL ? row_in_slice(P, row) : row;
     const float4 ic = __ldg(P.icst + i);      // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+    const float4 stp = __ldg(P.steps);        // {tau_u, sigma_q, sigma_p, 0}
 
     // TV dual: forward differences (Neumann), ascent, l2-ball projection
     const float gx = col + 1 < P.W ? xbar[o + P.k].x - xb.x : 0.0f;
     const float gy = yy + 1 < P.H ? xbar[o + static_cast<size_t>(P.W) * P.k].x - xb.x : 0.0f;
-    float px = d.z + P.sigma_p * gx;
-    float py = d.w + P.sigma_p * gy;
+    float px = d.z + stp.z * gx;
+    float py = d.w + stp.z * gy;
     float pzv = 0.0f;
     if (VOL) {
         const float gz = pix < P.N - P.HW ? xbar[o + static_cast<size_t>(P.HW) * P.k].x - xb.x
                                           : 0.0f;
-        pzv = pz[o] + P.sigma_p * gz;
+        pzv = pz[o] + stp.z * gz;
     }
     if (P.aniso) {                              // l-infinity box (anisotropic TV)
         px = fminf(fmaxf(px, -ic.w), ic.w);
@@ -136,7 +137,7 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
     const float tail = sc.total - sc.incl;
     float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
     float z = d.y + ic.z * xb.y;
-    if (i == 0) q[pix] -= P.sigma_q * (1.0f + P.delta * sc.total);
+    if (i == 0) q[pix] -= stp.y * (1.0f + P.delta * sc.total);
 
     // (v, z) onto Delta * epi(rho_i^*)
     float yo, ho;
@@ -184,6 +185,7 @@ __device__ __forceinline__ void dual_pair(const LiftParams &P, const float2 *__r
     const SegScan2 sc = block_segmented_scan2(make_float2(xb[0].y, xb[1].y), lp * P.k, P.k, tid,
                                               act[0], sm.in, sm.last);
     const float4 ic = __ldg(P.icst + (lp < P.ppb ? i : 0));  // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+    const float4 stp = __ldg(P.steps);                        // {tau_u, sigma_q, sigma_p, 0}
     float px[2], py[2], y0[2], h0[2];
     bool below[2];
 #pragma unroll
@@ -199,13 +201,13 @@ __device__ __forceinline__ void dual_pair(const LiftParams &P, const float2 *__r
         const float gx = col + 1 < P.W ? xbar[o[u] + P.k].x - xb[u].x : 0.0f;
         const float gy = yy + 1 < P.H ? xbar[o[u] + static_cast<size_t>(P.W) * P.k].x - xb[u].x
                                       : 0.0f;
-        px[u] = d[u].z + P.sigma_p * gx;
-        py[u] = d[u].w + P.sigma_p * gy;
+        px[u] = d[u].z + stp.z * gx;
+        py[u] = d[u].w + stp.z * gy;
         float pzv = 0.0f;
         if (VOL) {
             const float gz = pix[u] < P.N - P.HW
                                  ? xbar[o[u] + static_cast<size_t>(P.HW) * P.k].x - xb[u].x : 0.0f;
-            pzv = pz[o[u]] + P.sigma_p * gz;
+            pzv = pz[o[u]] + stp.z * gz;
         }
         if (P.aniso) {
             px[u] = fminf(fmaxf(px[u], -ic.w), ic.w);
@@ -227,7 +229,7 @@ __device__ __forceinline__ void dual_pair(const LiftParams &P, const float2 *__r
         const float tail = total - (u == 0 ? sc.incl.x : sc.incl.y);
         const float v = d[u].x + ic.z * (xb[u].x + P.delta * tail - ic.x * xb[u].y);
         const float z = d[u].y + ic.z * xb[u].y;
-        if (i == 0) q[pix[u]] -= P.sigma_q * (1.0f + P.delta * total);
+        if (i == 0) q[pix[u]] -= stp.y * (1.0f + P.delta * total);
         y0[u] = v * P.inv_delta;
         h0[u] = z * P.inv_delta;
         below[u] = !piece_in_epigraph<0>(P, pix[u], i, ic.x, y0[u], h0[u]);
@@ -285,6 +287,7 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     const int row = pixel_row(P, pix);
     const int col = pix - row * P.W;
     const float4 ic = __ldg(P.icst + i);
+    const float tau_u = __ldg(P.steps).x;
     const float qq = q[pix];
 
     // div p = -grad^T p (Neumann forward differences)
@@ -295,7 +298,7 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     if (row > 0) dv -= y[o - static_cast<size_t>(P.W) * P.k].w;
 
     const float head = sc.incl - d.x;             // sum of v over earlier intervals
-    const float un = fminf(fmaxf(xo.x - P.tau_u * (d.x - dv), 0.0f), 1.0f);
+    const float un = fminf(fmaxf(xo.x - tau_u * (d.x - dv), 0.0f), 1.0f);
     const float sn = xo.y - ic.y * (d.y - P.delta * qq + P.delta * head - ic.x * d.x);
     x[o] = make_float2(un, sn);
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
@@ -313,7 +316,7 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     __shared__ float s_in[kStepThreads];
     __shared__ float s_last[kStepThreads / 32];
     if (LIVE && *P.live == 0) return;
-    dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x, s_in, s_last, pz);
+    dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x + P.blk_off, s_in, s_last, pz);
 }
 
 // Quadratic pieces on an image with k >= kPairMinK: two tiles per block with
@@ -325,7 +328,7 @@ dual_pair_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
 {
     __shared__ PairSmem<kStepThreads> sm;
     if (LIVE && *P.live == 0) return;
-    dual_pair<kStepThreads, false>(P, xbar, y, q, nullptr, blockIdx.x, sm);
+    dual_pair<kStepThreads, false>(P, xbar, y, q, nullptr, blockIdx.x + P.blk_off, sm);
 }
 
 // Single-instance primal step: each block takes two consecutive tiles and
@@ -346,7 +349,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     int pix[2]; bool act[2]; size_t o[2]; float4 d[2]; float2 xo[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-        pix[u] = (2 * blockIdx.x + u) * P.ppb + lp;
+        pix[u] = (2 * (blockIdx.x + P.blk_off) + u) * P.ppb + lp;
         act[u] = lp < P.ppb && pix[u] < P.N;
         o[u] = static_cast<size_t>(pix[u]) * P.k + i;
         d[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -356,6 +359,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     const SegScan2 sc = block_segmented_scan2(make_float2(d[0].x, d[1].x), lp * P.k, P.k, tid,
                                               act[0] || act[1], s_in, s_last);
     const float4 ic = __ldg(P.icst + (lp < P.ppb ? i : 0));
+    const float tau_u = __ldg(P.steps).x;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (!act[u]) continue;
@@ -373,7 +377,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
             if (pix[u] >= P.HW) dv -= pz[o[u] - static_cast<size_t>(P.HW) * P.k];
         }
         const float head = (u == 0 ? sc.incl.x : sc.incl.y) - d[u].x;
-        const float un = fminf(fmaxf(xo[u].x - P.tau_u * (d[u].x - dv), 0.0f), 1.0f);
+        const float un = fminf(fmaxf(xo[u].x - tau_u * (d[u].x - dv), 0.0f), 1.0f);
         const float sn = xo[u].y - ic.y * (d[u].y - P.delta * qq + P.delta * head - ic.x * d[u].x);
         x[o[u]] = make_float2(un, sn);
         xbar[o[u]] = make_float2(2.0f * un - xo[u].x, 2.0f * sn - xo[u].y);
@@ -479,16 +483,28 @@ static inline int step_blocks(const LiftParams &P)
     return (P.N + P.ppb - 1) / P.ppb;
 }
 
-cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+// Which dual kernel a problem uses, and its unit (tiles per block).
+static inline bool dual_in_pairs(const LiftParams &P)
 {
-    // volumes never belong to a batch, so VOL and LIVE do not meet
-    const int nb = step_blocks(P), npair = (nb + 1) / 2;
+    return P.kind != 2 && P.D == 1 && P.k >= kPairMinK;
+}
+
+// Dual half-step on the tiles [t0, t1).
+cudaError_t launch_dual_band(const LiftParams &P0, const LiftState &S, int t0, int t1,
+                             cudaStream_t st)
+{
+    LiftParams P = P0;
     const bool vol = P.D > 1, live = P.live != nullptr;
-    if (P.kind != 2 && !vol && P.k >= kPairMinK) {
-        if (live) dual_pair_kernel<true><<<npair, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
-        else dual_pair_kernel<false><<<npair, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+    if (dual_in_pairs(P)) {
+        // volumes never belong to a batch, so VOL and LIVE do not meet
+        P.blk_off = t0 / 2;
+        const int nb = (t1 - t0 + 1) / 2;
+        if (live) dual_pair_kernel<true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
+        else dual_pair_kernel<false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
         return cudaGetLastError();
     }
+    P.blk_off = t0;
+    const int nb = t1 - t0;
     if (P.kind == 2) {
         if (vol) dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
         else if (live) dual_step_kernel<2, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
@@ -501,9 +517,13 @@ cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+// Primal half-step on the tiles [t0, t1) (two tiles per block).
+cudaError_t launch_primal_band(const LiftParams &P0, const LiftState &S, int t0, int t1,
+                               cudaStream_t st)
 {
-    const int nb = (step_blocks(P) + 1) / 2;
+    LiftParams P = P0;
+    P.blk_off = t0 / 2;
+    const int nb = (t1 - t0 + 1) / 2;
     if (P.D > 1)
         primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz);
     else if (P.live != nullptr)
@@ -511,6 +531,16 @@ cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStre
     else
         primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+{
+    return launch_dual_band(P, S, 0, step_blocks(P), st);
+}
+
+cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st)
+{
+    return launch_primal_band(P, S, 0, step_blocks(P), st);
 }
 
 }  // namespace lift

@@ -213,14 +213,16 @@ cudaLaunchConfig_t resident_config(const ResidentPlan &R, cudaStream_t st,
     return cfg;
 }
 
+// The attributes belong to the kernel, not to a handle: they are set to the
+// largest request of any handle (every launch asks for at most
+// kResidentMaxSmem bytes), so that handles of different sizes can alternate.
 template <int KIND>
 bool resident_fits(ResidentPlan &R)
 {
     if (cudaFuncSetAttribute(resident_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(R.smem)) != cudaSuccess ||
-        (R.ctas > 8 && cudaFuncSetAttribute(resident_kernel<KIND>,
-                                            cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                            1) != cudaSuccess)) {
+                             static_cast<int>(kResidentMaxSmem)) != cudaSuccess ||
+        cudaFuncSetAttribute(resident_kernel<KIND>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }

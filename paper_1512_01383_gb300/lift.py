@@ -31,7 +31,7 @@ EXPORTED = (
     "lift_batch_get_state", "lift_batch_autotune", "lift_batch_schedule",
     "lift_batch_set_schedule",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
-    "lift_get_balance", "lift_set_resident",
+    "lift_get_balance", "lift_set_resident", "lift_set_bands",
 )
 
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "lift_unrolled_backward": (C.c_int, [vp, vp, vp, dp]),
         "lift_get_balance": (C.c_int, [vp, dp]),
         "lift_set_resident": (C.c_int, [vp, C.c_int, ip]),
+        "lift_set_bands": (C.c_int, [vp, C.c_int, ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +191,13 @@ def lift_get_balance(h: int) -> float:
     t = C.c_double()
     _check(load().lift_get_balance(C.c_void_p(h), C.byref(t)), "lift_get_balance")
     return t.value
+
+
+def lift_set_bands(h: int, bands: int) -> int:
+    """Bands of the iteration graph (0 automatic, 1 off); returns the number used."""
+    u = C.c_int()
+    _check(load().lift_set_bands(C.c_void_p(h), bands, C.byref(u)), "lift_set_bands")
+    return u.value
 
 
 def lift_set_resident(h: int, enable: bool) -> bool:

@@ -325,8 +325,9 @@ def test_graph_replay_equals_direct_launches():
         np.testing.assert_array_equal(a.unlift(), b.unlift())
 
 
+@pytest.mark.parametrize("resident", [True, False])
 @pytest.mark.parametrize("L", [5, 10])
-def test_adaptive_balance_matches_oracle(L):
+def test_adaptive_balance_matches_oracle(L, resident):
     """lift_solve with adaptive_balance re-balances theta at every check from
     the movement since the previous check; the same rule on the oracle gives
     the same theta sequence and iterate."""
@@ -336,7 +337,7 @@ def test_adaptive_balance_matches_oracle(L):
     P = oracle_problem(c)
     X = O.State(P)
     th_o = O.pdhg_adaptive(P, X, 5, 100)
-    with gpu_solver(c, check_every=100, adaptive_balance=True) as s:
+    with gpu_solver(c, check_every=100, adaptive_balance=True, resident=resident) as s:
         rc, n = s.solve(500, 1e-15)
         assert rc == G.LIFT_ERR_NOT_CONVERGED and n == 500
         th_g = G.lift_get_balance(s.h)

@@ -109,3 +109,27 @@ def test_resident_solve_reaches_gap():
             assert rc == G.LIFT_OK and s.gap() <= 1e-5
             its.append(n)
     assert abs(its[0] - its[1]) <= 200, its
+
+
+def test_resident_handles_of_different_sizes_alternate():
+    """Handles with different shared-memory needs, created in turn and then
+    iterated alternately, all take the resident path and match their
+    per-half-step twins."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    shapes = [(64, 64, 2), (19, 17, 20), (40, 40, 6), (13, 11, 3)]
+    cases = [case(1 if L > 2 else 0, H, W, L, 3300 + j) for j, (H, W, L) in enumerate(shapes)]
+    res = [gpu_solver(c) for c in cases]
+    ref = [gpu_solver(c, resident=False) for c in cases]
+    try:
+        assert all(G.lift_set_resident(s.h, True) for s in res)
+        for _ in range(3):
+            for s, r in zip(res, ref):
+                s.iterate(20)
+                r.iterate(20)
+        for s, r, c in zip(res, ref, cases):
+            rng = c["gamma_max"] - c["gamma_min"]
+            assert np.abs(s.unlift() - r.unlift()).max() / rng <= U_TOL
+    finally:
+        for s in res + ref:
+            s.close()
