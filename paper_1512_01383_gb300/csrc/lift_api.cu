@@ -656,8 +656,10 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
 int lift_set_bands(lift_handle h, int bands, int *used)
 {
     if (!h || bands < 0) return LIFT_ERR_ARG;
-    h->bands_req = bands;
-    drop_iter_graph(h);
+    if (bands != h->bands_req) {
+        h->bands_req = bands;
+        drop_iter_graph(h);
+    }
     if (used) *used = bands_used(h);
     return LIFT_OK;
 }
