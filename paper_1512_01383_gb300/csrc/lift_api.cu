@@ -773,6 +773,8 @@ const char *lift_strerror(int code)
 // on the single-instance kernels (skipped through its live flag once
 // converged).  Every check interval is captured in one CUDA graph.
 // ===========================================================================
+constexpr int kBatchStreams = 4;
+
 struct lift_batch_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -798,6 +800,10 @@ struct lift_batch_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_iters = 0;
+    // the big instances of a captured interval run on these streams (forked
+    // from and joined back into `stream`), several instances at once
+    cudaStream_t fork_s[kBatchStreams] = {};
+    cudaEvent_t fork_e[kBatchStreams + 1] = {};
 };
 
 namespace {
@@ -821,6 +827,10 @@ void free_batch(lift_batch b)
         if (p) cudaFree(p);
     if (b->hout) cudaFreeHost(b->hout);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    for (cudaStream_t st : b->fork_s)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->fork_e)
+        if (ev) cudaEventDestroy(ev);
     delete b;
 }
 
@@ -905,11 +915,46 @@ int batch_launch(lift_batch b, int iters)
     return LIFT_OK;
 }
 
+// In a captured interval the merged launches stay on the batch stream and
+// the big instances, which share nothing, are spread over kBatchStreams
+// forked streams (all their iterations back to back), so that the dual steps
+// of one instance run beside the primal steps of another.
+int batch_launch_forked(lift_batch b, int iters)
+{
+    if (b->big.empty()) return batch_launch(b, iters);
+    if (!b->fork_s[0]) {
+        for (int j = 0; j < kBatchStreams; ++j)
+            LIFT_CK(cudaStreamCreateWithFlags(&b->fork_s[j], cudaStreamNonBlocking));
+        for (int j = 0; j <= kBatchStreams; ++j)
+            LIFT_CK(cudaEventCreateWithFlags(&b->fork_e[j], cudaEventDisableTiming));
+    }
+    const int ns = std::min(kBatchStreams, static_cast<int>(b->big.size()));
+    LIFT_CK(cudaEventRecord(b->fork_e[kBatchStreams], b->stream));
+    for (int j = 0; j < ns; ++j) LIFT_CK(cudaStreamWaitEvent(b->fork_s[j], b->fork_e[kBatchStreams], 0));
+    for (int it = 0; it < iters; ++it)
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->pair_inst,
+                                             b->single_inst, b->live, b->total_tiles,
+                                             b->total_pairs, b->total_singles, b->stream));
+    for (size_t m = 0; m < b->big.size(); ++m) {
+        cudaStream_t st = b->fork_s[m % ns];
+        const LiftState &S = b->S[b->big[m]];
+        for (int it = 0; it < iters; ++it) {
+            LIFT_CK(lift::launch_dual_step(b->Pbig[m], S, st));
+            LIFT_CK(lift::launch_primal_step(b->Pbig[m], S, st));
+        }
+    }
+    for (int j = 0; j < ns; ++j) {
+        LIFT_CK(cudaEventRecord(b->fork_e[j], b->fork_s[j]));
+        LIFT_CK(cudaStreamWaitEvent(b->stream, b->fork_e[j], 0));
+    }
+    return LIFT_OK;
+}
+
 int batch_capture(lift_batch b, int iters)
 {
     drop_graph(b);
     LIFT_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = batch_launch(b, iters);
+    const int rc = batch_launch_forked(b, iters);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rc != LIFT_OK || e != cudaSuccess) {
