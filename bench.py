@@ -637,7 +637,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
                     "d2h_bytes_per_step": H * W * 4 + 24},
-            "gpu_launches": args.steps * (2 * ITERS_PER_STEP + 3),
+            # per iteration one dual and one primal launch per band, then the
+            # energy, its finish and the unlift per step
+            "gpu_launches": args.steps * (2 * bands * ITERS_PER_STEP + 3),
             "clocks": clk.summary(),
             "time_to_gap_1e-5": ttg or None,
             "batch": batch,
