@@ -61,7 +61,8 @@ __device__ __forceinline__ void res_dual_tile(const LiftParams &P, ResMem &M,
                                               float *s_last)
 {
     // the previous tile's scan results may still be read from s_in / s_last
-    __syncthreads();
+    // (the first tile of a phase follows a cluster barrier)
+    if (lt > 0) __syncthreads();
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
@@ -76,7 +77,9 @@ __device__ __forceinline__ void res_dual_tile(const LiftParams &P, ResMem &M,
         xb = M.xb[lo];
         d = M.y[lo];
     }
-    const SegScan sc = block_segmented_scan(xb.y, lp * P.k, P.k, tid, active, s_in, s_last);
+    // with one interval per pixel every segment is a single record
+    const SegScan sc = P.k == 1 ? SegScan{xb.y, xb.y}
+                                : block_segmented_scan(xb.y, lp * P.k, P.k, tid, active, s_in, s_last);
     if (!active) return;
 
     const int row = pixel_row(P, pix);
@@ -113,7 +116,7 @@ __device__ __forceinline__ void res_primal_tile(const LiftParams &P, ResMem &M,
                                                 cg::cluster_group &cl, int lt, float *s_in,
                                                 float *s_last)
 {
-    __syncthreads();                            // as in res_dual_tile
+    if (lt > 0) __syncthreads();                // as in res_dual_tile
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
@@ -128,7 +131,8 @@ __device__ __forceinline__ void res_primal_tile(const LiftParams &P, ResMem &M,
         d = M.y[lo];
         xo = M.x[lo];
     }
-    const SegScan sc = block_segmented_scan(d.x, lp * P.k, P.k, tid, active, s_in, s_last);
+    const SegScan sc = P.k == 1 ? SegScan{d.x, d.x}
+                                : block_segmented_scan(d.x, lp * P.k, P.k, tid, active, s_in, s_last);
     if (!active) return;
 
     const int row = pixel_row(P, pix);
