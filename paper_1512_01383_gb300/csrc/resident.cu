@@ -41,6 +41,20 @@ struct ResMem {
 
 __device__ __forceinline__ int res_owner(const ResMem &M, int pix) { return pix / M.ppc; }
 
+// The cluster barrier in its two halves: every thread arrives when its CTA's
+// writes of a phase are done (release), and waits (acquire) only where it is
+// about to read another CTA's shared memory or to overwrite what others read,
+// so that its own loads and scan overlap the barrier.
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ float2 res_xbar(const ResMem &M, cg::cluster_group &cl, int pix, int i)
 {
     const int c = res_owner(M, pix);
@@ -80,6 +94,9 @@ __device__ __forceinline__ void res_dual_tile(const LiftParams &P, ResMem &M,
     // with one interval per pixel every segment is a single record
     const SegScan sc = P.k == 1 ? SegScan{xb.y, xb.y}
                                 : block_segmented_scan(xb.y, lp * P.k, P.k, tid, active, s_in, s_last);
+    // before the first read of another CTA's xbar (and this phase's writes of
+    // y, which the other CTAs read in the previous phase)
+    if (lt == 0) cluster_wait();
     if (!active) return;
 
     const int row = pixel_row(P, pix);
@@ -133,6 +150,7 @@ __device__ __forceinline__ void res_primal_tile(const LiftParams &P, ResMem &M,
     }
     const SegScan sc = P.k == 1 ? SegScan{d.x, d.x}
                                 : block_segmented_scan(d.x, lp * P.k, P.k, tid, active, s_in, s_last);
+    if (lt == 0) cluster_wait();                 // as in res_dual_tile
     if (!active) return;
 
     const int row = pixel_row(P, pix);
@@ -180,15 +198,21 @@ resident_kernel(const LiftParams P, LiftState S, int iters, int ppc)
         M.xb[r] = S.xbar[g0 + r];
     }
     for (int r = tid; r < M.npx; r += kStepThreads) M.q[r] = S.q[M.p0 + r];
-    cl.sync();
+    // the state is in place; each phase's first tile waits for this (or the
+    // previous phase's) arrival of every thread of the cluster
+    __syncthreads();
+    cluster_arrive();
 
     const int ntl = (M.npx + P.ppb - 1) / P.ppb;
     for (int it = 0; it < iters; ++it) {
         for (int lt = 0; lt < ntl; ++lt) res_dual_tile<KIND>(P, M, cl, lt, s_in, s_last);
-        cl.sync();
+        __syncthreads();
+        cluster_arrive();
         for (int lt = 0; lt < ntl; ++lt) res_primal_tile(P, M, cl, lt, s_in, s_last);
-        cl.sync();
+        __syncthreads();
+        cluster_arrive();
     }
+    cluster_wait();
 
     // every remote read of this CTA's state ended at the last cluster barrier
     for (int r = tid; r < n; r += kStepThreads) {
