@@ -101,6 +101,8 @@ def test_null_arguments(lib):
     assert L.lift_batch_schedule(None, None, None, None) == lib.LIFT_ERR_ARG
     assert L.lift_batch_size(None) == 0
     L.lift_batch_destroy(None)
+    assert L.lift_set_bands(None, 0, None) == lib.LIFT_ERR_ARG
+    assert L.lift_set_resident(None, 1, None) == lib.LIFT_ERR_ARG
 
 
 def test_volume_batch_rejected_before_any_cuda_call(lib):
