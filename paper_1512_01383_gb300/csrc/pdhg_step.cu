@@ -334,9 +334,11 @@ dual_pair_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
 // Single-instance primal step: each block takes two consecutive tiles and
 // issues the loads of both before the (shared) scan, doubling the bytes in
 // flight per thread; the primal step waits on memory rather than on issue.
-// The neighbours' p (x-1, y-1) and q are loaded before the scan's barrier
-// too, so their latency overlaps it (37.3 -> 34.9 us per launch at 512^2,
-// L = 20, same registers).
+// On images the neighbours' p (x-1, y-1) and q are loaded before the scan's
+// barrier too, so their latency overlaps it (37.3 -> 34.9 us per launch at
+// 512^2, L = 20, same registers; on a volume that took 40 -> 46 registers
+// and one block per SM, 117 -> 129 us at 128^3, L = 8, so volumes load them
+// after the scan).
 template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
@@ -352,6 +354,14 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     int pix[2]; bool act[2]; size_t o[2]; float4 d[2]; float2 xo[2];
     int col[2], yy[2];
     float qq[2], px_left[2], py_up[2];   // q and the neighbours' p at x-1, y-1
+    auto neighbours = [&](int u) {
+        const int row = pixel_row(P, pix[u]);
+        col[u] = pix[u] - row * P.W;
+        yy[u] = VOL ? row_in_slice(P, row) : row;
+        qq[u] = q[pix[u]];
+        if (col[u] > 0) px_left[u] = y[o[u] - P.k].z;
+        if (yy[u] > 0) py_up[u] = y[o[u] - static_cast<size_t>(P.W) * P.k].w;
+    };
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         pix[u] = (2 * (blockIdx.x + P.blk_off) + u) * P.ppb + lp;
@@ -364,12 +374,9 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
         if (act[u]) {
             d[u] = y[o[u]];
             xo[u] = x[o[u]];
-            const int row = pixel_row(P, pix[u]);
-            col[u] = pix[u] - row * P.W;
-            yy[u] = VOL ? row_in_slice(P, row) : row;
-            qq[u] = q[pix[u]];
-            if (col[u] > 0) px_left[u] = y[o[u] - P.k].z;
-            if (yy[u] > 0) py_up[u] = y[o[u] - static_cast<size_t>(P.W) * P.k].w;
+            // images: the neighbours' loads overlap the scan's barrier; on a
+            // volume the extra live registers would cost a block per SM
+            if (!VOL) neighbours(u);
         }
     }
     const SegScan2 sc = block_segmented_scan2(make_float2(d[0].x, d[1].x), lp * P.k, P.k, tid,
@@ -379,6 +386,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         if (!act[u]) continue;
+        if (VOL) neighbours(u);
         // div p = -grad^T p (Neumann forward differences)
         float dv = 0.0f;
         if (col[u] + 1 < P.W) dv += d[u].z;
