@@ -57,3 +57,17 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(argparse.Namespace(steps=1, warmup=0)) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_all_cores_oracle_leg_runs_every_worker():
+    """The all-cores CPU leg of bench.py: spawned workers, each running the
+    unmodified oracle on its own crop; the throughput counts every worker's
+    units over the wall time of the whole map."""
+    sys.path.insert(0, ROOT)
+    import bench
+    f = bench.make_input(0)
+    n, reps = bench.cpu_sample_all_cores(f, 24, 3, reps=2, workers=2)
+    assert n == 2 and len(reps) == 2
+    for value, wall in reps:
+        assert wall > 0 and value > 0
+        assert abs(value - 2 * 24 * 24 * bench.K_INT * 3 / wall / 1e9) <= 1e-12 * value
