@@ -1,0 +1,41 @@
+"""Worked examples with hand-derived values (tests/golden/, each file citing
+the passage it follows): the oracle must reproduce them.  The same
+two-pixel problems run on the GPU in test_gpu_parity."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name: str) -> np.ndarray:
+    return np.atleast_2d(np.loadtxt(os.path.join(GOLDEN, name), comments="#"))
+
+
+@pytest.mark.parametrize("row", list(golden("rof_two_pixel.txt")))
+def test_two_pixel_rof_closed_form(row):
+    """L = 2 (Prop. 3) on two pixels: at convergence the lifted iterate
+    unlifts to the soft-thresholded pair and every energy bound meets the
+    closed-form optimum."""
+    f1, f2, lam, u1, u2, E = row
+    P = O.Problem(O.QUAD, 1, 2, 2, 0.0, 1.0, lam=lam, alpha=1.0, f=np.array([f1, f2]))
+    X = O.State(P)
+    O.pdhg(P, X, 20000)
+    ut = O.unlift(P, X.u)
+    assert np.abs(ut - [u1, u2]).max() <= 1e-7, ut
+    Ph, D, Enc = O.energy(P, X)
+    assert D <= E + 1e-9 and Ph >= E - 1e-9          # weak duality around the optimum
+    for v in (Ph, D, Enc):
+        assert abs(v - E) <= 1e-7, (v, E)
+
+
+@pytest.mark.parametrize("row", list(golden("quad_piece_conjugate.txt")))
+def test_quadratic_piece_conjugate(row):
+    f, alpha, L, i, y, c, t = row
+    P = O.Problem(O.QUAD, 1, 1, int(L), 0.0, 1.0, alpha=alpha, f=np.array([f]))
+    val, arg = O.conj(P, 0, int(i), y)
+    assert abs(val - c) <= 1e-12, (val, c)
+    assert abs(arg - t) <= 1e-12, (arg, t)

@@ -410,3 +410,23 @@ def test_baseline_lifting_matches_oracle(L, iters):
     Po, Do, Eo = O.energy(P, X)
     for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
         assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
+
+
+@pytest.mark.parametrize("resident", [True, False])
+def test_two_pixel_rof_golden(resident):
+    """The hand-derived two-pixel closed forms of tests/golden/rof_two_pixel.txt
+    (L = 2, Prop. 3) on the GPU: after 20 000 iterations the unlifted pair
+    and the energies meet them within FP32 rounding."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    from test_golden import golden
+    for f1, f2, lam, u1, u2, E in golden("rof_two_pixel.txt"):
+        f = torch.tensor([[f1, f2]], dtype=torch.float32, device="cuda")
+        with G.Solver(G.LIFT_QUAD, 1, 2, 2, 0.0, 1.0, lam, 1.0, 0.0, f=f,
+                      resident=resident) as s:
+            s.iterate(20000)
+            ut = s.unlift().reshape(-1)
+            Pg, Dg, Eg = s.energy()
+        assert np.abs(ut - [u1, u2]).max() <= 2e-6, (ut, u1, u2)
+        for v in (Pg, Dg, Eg):
+            assert abs(v - E) <= 1e-6, (v, E)
