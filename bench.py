@@ -594,6 +594,18 @@ def main():
                 * args.steps / (ms * 1e-3) / 1e9)
     dual_gbs = DUAL_BYTES_PER_PIX * H * W / (dual_ms * 1e-3) / 1e9
     primal_gbs = PRIMAL_BYTES_PER_PIX * H * W / (primal_ms * 1e-3) / 1e9
+    # the iterations alone (graph replays, no gap check or unlift): the
+    # median of 5 replays of 10 check intervals, events on the same stream
+    reps = []
+    for _ in range(5):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        solver.iterate(10 * ITERS_PER_STEP)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        reps.append(a0.elapsed_time(a1) / (10 * ITERS_PER_STEP))
+    iter_only_ms = statistics.median(reps)
+    iter_only_gbs = (DUAL_BYTES_PER_PIX + PRIMAL_BYTES_PER_PIX) * H * W / (iter_only_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers: upload f from pinned
     # host memory, reset, iterate, gap check, unlift to host
@@ -691,6 +703,10 @@ def main():
                          # others, so this exceeds the isolated kernels' rates
                          "iteration": {"achieved": iter_gbs, "frac": iter_gbs / peak,
                                        "bands": bands,
+                                       # graph replays of the iterations alone
+                                       "iterations_only": {"achieved": iter_only_gbs,
+                                                           "frac": iter_only_gbs / peak,
+                                                           "us_per_iteration": iter_only_ms * 1e3},
                                        "algorithmic_bytes_per_iteration":
                                            (DUAL_BYTES_PER_PIX + PRIMAL_BYTES_PER_PIX) * H * W}},
             "cpu_baseline": cpu,
