@@ -53,7 +53,7 @@ PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
 # DRAM bytes per dual-step launch from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), profiles/dual_step_trunc512_L20.md; None when the
 # kernel has changed since the capture.
-DUAL_TRAFFIC_NCU = 149113600
+DUAL_TRAFFIC_NCU = 149163008
 PEAK_FALLBACK_GBS = 6800.0
 
 
