@@ -33,11 +33,8 @@
 
 namespace lift {
 
-// One tile: floor(THREADS/k) whole pixels of one problem instance, one
-// thread per (pixel, interval) record.  Shared by the single-instance kernels
-// and the batched kernels of lift_batch.cu.
-// The same segmented scan for two independent values per thread (two tiles
-// of the same shape processed by one block), one barrier for both.
+// The segmented scan of lift_tile.cuh for two independent values per thread
+// (two tiles of the same shape processed by one block), one barrier for both.
 struct SegScan2 {
     float2 incl, total;
 };
@@ -77,8 +74,11 @@ __device__ __forceinline__ SegScan2 block_segmented_scan2(float2 val, int seg, i
     return r;
 }
 
-// VOL: a D x H x W volume, whose p_i has a third component in pz (Sec. 4 on
-// the d = 3 grid); images take VOL = false and never touch pz.
+// One tile: floor(THREADS/k) whole pixels of one problem instance, one
+// thread per (pixel, interval) record; used by the single-instance kernels and
+// the batched kernels below.  VOL: a D x H x W volume, whose p_i has a third
+// component in pz (Sec. 4 on the d = 3 grid); images take VOL = false and
+// never touch pz.
 template <int KIND, int THREADS, bool VOL = false>
 __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__restrict__ xbar,
                                           float4 *__restrict__ y, float *__restrict__ q,
