@@ -25,7 +25,7 @@
  *     of d = 2 (image) or d = 3 (volume) axes, p_i in R^d),
  *     with the diagonal preconditioning of Pock-Chambolle (alpha = 1).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   c_i(v) = <1_{i-1}, v> - gamma_i v_i / Delta_i (appendix form, proof of
  *   Prop. 1); lambda is the radius factor of K (|p_i| <= lambda*Delta_i);
  *   Neumann forward differences; primal box u in [0,1]^k; fixed steps
