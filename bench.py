@@ -53,9 +53,8 @@ WORKLOAD = ("truncated-quadratic denoising 512x512, L=20 (k=19), alpha=25 nu=0.1
 DUAL_BYTES_PER_PIX = 40 * K_INT + 12
 PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
 # DRAM bytes per dual-step launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), profiles/dual_step_trunc512_L20.md; None when the
-# kernel has changed since the capture.
-DUAL_TRAFFIC_NCU = 149163008
+# dram__bytes_write.sum); None while no capture of the current kernel exists.
+DUAL_TRAFFIC_NCU = None
 PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -690,7 +689,7 @@ def main():
             "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "k": K_INT,
                        "iters_per_step": ITERS_PER_STEP, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (160 MB state, 403 MB per iteration)"},
-            "roofline": {"bound": "hbm", "kernel": "dual_pair_kernel (dual step)", "achieved": dual_gbs,
+            "roofline": {"bound": "hbm", "kernel": "dual_strip_kernel (dual step)", "achieved": dual_gbs,
                          "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                          "frac": dual_gbs / peak, "traffic": DUAL_TRAFFIC_NCU,
                          "algorithmic_bytes_per_launch": DUAL_BYTES_PER_PIX * H * W,

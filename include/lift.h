@@ -44,6 +44,10 @@ extern "C" {
 #define LIFT_ERR_NAN            4  /* non-finite energy: iterate diverged   */
 #define LIFT_ERR_NOT_CONVERGED  5  /* max_iters reached before gap <= tol   */
 #define LIFT_ERR_ARG            6  /* invalid argument (null, size, range)  */
+#define LIFT_ERR_TIMEOUT        7  /* a kernel's bounded wait for its bulk
+                                      copies gave up; the iterate is invalid
+                                      (reported by the next lift_energy /
+                                      lift_gap / lift_solve check)          */
 
 /* Largest supported number of label intervals k = L-1. */
 #define LIFT_MAX_K 64

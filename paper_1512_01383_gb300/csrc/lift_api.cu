@@ -376,8 +376,9 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     ALLOC(h->steps, sizeof(float4));
     ALLOC(h->ubuf, N * sizeof(float));
     ALLOC(h->partial, 3 * sizeof(double) * lift::energy_blocks(P));
-    ALLOC(h->dout, 3 * sizeof(double));
-    if (cudaMallocHost(reinterpret_cast<void **>(&h->hout), 3 * sizeof(double)) != cudaSuccess) {
+    // three energy sums and, in the fourth slot, the kernels' error word
+    ALLOC(h->dout, 4 * sizeof(double));
+    if (cudaMallocHost(reinterpret_cast<void **>(&h->hout), 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         h->hout = nullptr;
         free_ctx(h);
@@ -398,6 +399,8 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
         ALLOC(h->f, N * sizeof(float));
     }
 #undef ALLOC
+    CUDA_OR_FAIL(cudaMemsetAsync(h->dout, 0, 4 * sizeof(double), h->stream));
+    P.err = reinterpret_cast<int *>(h->dout + 3);
     P.icst = h->icst;
     P.steps = h->steps;
     P.f = h->f;
@@ -601,9 +604,12 @@ int lift_energy(lift_handle h, double *primal_relaxed, double *dual, double *e_n
 {
     if (!h) return LIFT_ERR_ARG;
     LIFT_CK(lift::launch_energy(h->P, h->S, h->partial, h->dout, h->stream));
-    LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+    LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
     LIFT_CK(cudaStreamSynchronize(h->stream));
+    int err_word = 0;
+    memcpy(&err_word, h->hout + 3, sizeof(int));
+    if (err_word != 0) return LIFT_ERR_TIMEOUT;
     if (primal_relaxed) *primal_relaxed = h->hout[0];
     if (dual) *dual = h->hout[1];
     if (e_nonconvex) *e_nonconvex = h->hout[2];
@@ -760,6 +766,7 @@ const char *lift_strerror(int code)
     case LIFT_ERR_NAN: return "non-finite energy (iterate diverged)";
     case LIFT_ERR_NOT_CONVERGED: return "gap tolerance not reached within max_iters";
     case LIFT_ERR_ARG: return "invalid argument";
+    case LIFT_ERR_TIMEOUT: return "a kernel's bounded wait for its bulk copies gave up";
     default: return "unknown error code";
     }
 }
@@ -789,9 +796,10 @@ struct lift_batch_ctx {
     void *arena = nullptr;              // all per-instance device arrays
     lift::InstDesc *desc = nullptr;     // device [n]
     int *tile_inst = nullptr;           // device [total tiles]: instance of each tile
-    int *pair_inst = nullptr;           // device [total pairs]: dual step in tile pairs
-    int *single_inst = nullptr;         // device [total singles]: dual step in single tiles
-    int total_tiles = 0, total_pairs = 0, total_singles = 0;
+    int *strip_inst = nullptr;          // device [total strips]: instance of each dual strip
+    int total_tiles = 0, total_strips = 0;
+    int strip_stage = 0;                // shared bytes of the largest merged strip stage
+    int *err = nullptr;                 // device: set by a kernel whose bounded wait gave up
     int *live = nullptr;                // device [n]: 1 = still iterating
     std::vector<int> live_h;
     std::vector<long long> iters_h;     // iterations done per instance
@@ -821,8 +829,8 @@ void free_batch(lift_batch b)
 {
     if (!b) return;
     drop_graph(b);
-    void *ptrs[] = {b->arena, b->desc, b->tile_inst, b->pair_inst, b->single_inst, b->live,
-                    b->partial, b->dout, b->ubuf};
+    void *ptrs[] = {b->arena, b->desc, b->tile_inst, b->strip_inst, b->live,
+                    b->partial, b->dout, b->ubuf, b->err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->hout) cudaFreeHost(b->hout);
@@ -840,14 +848,15 @@ void free_batch(lift_batch b)
 int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 {
     std::vector<lift::InstDesc> d(b->n);
-    std::vector<int> ti, pi, si;
-    int t0 = 0;
+    std::vector<int> ti, si;
+    int t0 = 0, stage = 0;
     b->big.clear();
     b->Pbig.clear();
     for (int j = 0; j < b->n; ++j) {
         LiftParams Ps = b->P[j];
         Ps.ppb = lift::kStepThreads / Ps.k;
         Ps.live = b->live + j;
+        Ps.err = b->err;
         const int nt_single = (Ps.N + Ps.ppb - 1) / Ps.ppb;
         b->P[j].ppb = threads / b->P[j].k;
         const int nt = (b->P[j].N + b->P[j].ppb - 1) / b->P[j].ppb;
@@ -857,43 +866,40 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
             b->big.push_back(j);
             b->Pbig.push_back(Ps);
             b->ntiles[j] = 0;
-            d[j].tile0 = d[j].ntiles = d[j].pair0 = d[j].npairs = 0;
+            d[j].tile0 = d[j].ntiles = d[j].strip0 = d[j].nstrips = 0;
             continue;
         }
         b->ntiles[j] = nt;
         d[j].tile0 = t0;
         d[j].ntiles = nt;
-        std::vector<int> &ul = b->P[j].k >= lift::kPairMinK ? pi : si;
-        d[j].pair0 = static_cast<int>(ul.size());
-        d[j].npairs = b->P[j].k >= lift::kPairMinK ? (nt + 1) / 2 : nt;
+        // dual strips of kBatchStripThreads / T pixels (T threads per pixel)
+        const int sp = lift::kBatchStripThreads >> (d[j].P.k >= 12 ? 2 : (d[j].P.k >= 6 ? 1 : 0));
+        d[j].strip0 = static_cast<int>(si.size());
+        d[j].nstrips = (d[j].P.N + sp - 1) / sp;
+        stage = std::max(stage, lift::batch_strip_stage(d[j].P.k));
         ti.insert(ti.end(), nt, j);
-        ul.insert(ul.end(), d[j].npairs, j);
+        si.insert(si.end(), d[j].nstrips, j);
         t0 += nt;
     }
-    const int np = static_cast<int>(pi.size()), ns = static_cast<int>(si.size());
+    const int ns = static_cast<int>(si.size());
     if (ti.empty()) ti.push_back(0);    // keep valid allocations; the totals stay 0
-    if (pi.empty()) pi.push_back(0);
     if (si.empty()) si.push_back(0);
     if (b->tile_inst) cudaFree(b->tile_inst);
-    if (b->pair_inst) cudaFree(b->pair_inst);
-    if (b->single_inst) cudaFree(b->single_inst);
-    b->tile_inst = b->pair_inst = b->single_inst = nullptr;
+    if (b->strip_inst) cudaFree(b->strip_inst);
+    b->tile_inst = b->strip_inst = nullptr;
     int rc = dev_alloc(reinterpret_cast<void **>(&b->tile_inst), ti.size() * sizeof(int));
-    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->pair_inst), pi.size() * sizeof(int));
-    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->single_inst), si.size() * sizeof(int));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->strip_inst), si.size() * sizeof(int));
     if (rc != LIFT_OK) return rc;
     LIFT_CK(cudaMemcpyAsync(b->tile_inst, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b->stream));
-    LIFT_CK(cudaMemcpyAsync(b->pair_inst, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice,
-                            b->stream));
-    LIFT_CK(cudaMemcpyAsync(b->single_inst, si.data(), si.size() * sizeof(int),
+    LIFT_CK(cudaMemcpyAsync(b->strip_inst, si.data(), si.size() * sizeof(int),
                             cudaMemcpyHostToDevice, b->stream));
     LIFT_CK(cudaMemcpyAsync(b->desc, d.data(), d.size() * sizeof(lift::InstDesc),
                             cudaMemcpyHostToDevice, b->stream));
     LIFT_CK(cudaStreamSynchronize(b->stream));   // host vectors die here
     b->total_tiles = t0;
-    b->total_pairs = np;
-    b->total_singles = ns;
+    b->total_strips = ns;
+    b->strip_stage = stage;
     b->threads = threads;
     b->big_tiles = big_tiles;
     drop_graph(b);
@@ -903,9 +909,9 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 int batch_launch(lift_batch b, int iters)
 {
     for (int it = 0; it < iters; ++it) {
-        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->pair_inst,
-                                             b->single_inst, b->live, b->total_tiles,
-                                             b->total_pairs, b->total_singles, b->stream));
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->strip_inst,
+                                             b->live, b->total_tiles, b->total_strips,
+                                             b->strip_stage, b->err, b->stream));
         for (size_t m = 0; m < b->big.size(); ++m) {
             const LiftState &S = b->S[b->big[m]];
             LIFT_CK(lift::launch_dual_step(b->Pbig[m], S, b->stream));
@@ -932,9 +938,9 @@ int batch_launch_forked(lift_batch b, int iters)
     LIFT_CK(cudaEventRecord(b->fork_e[kBatchStreams], b->stream));
     for (int j = 0; j < ns; ++j) LIFT_CK(cudaStreamWaitEvent(b->fork_s[j], b->fork_e[kBatchStreams], 0));
     for (int it = 0; it < iters; ++it)
-        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->pair_inst,
-                                             b->single_inst, b->live, b->total_tiles,
-                                             b->total_pairs, b->total_singles, b->stream));
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->strip_inst,
+                                             b->live, b->total_tiles, b->total_strips,
+                                             b->strip_stage, b->err, b->stream));
     for (size_t m = 0; m < b->big.size(); ++m) {
         cudaStream_t st = b->fork_s[m % ns];
         const LiftState &S = b->S[b->big[m]];
@@ -1030,6 +1036,9 @@ int lift_create_batch(const lift_spec *specs, int n, void *stream, lift_batch *o
     if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->partial), 3 * sizeof(double) * max_eblocks);
     if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->dout), 3 * sizeof(double) * n);
     if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->ubuf), max_n * sizeof(float));
+    if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->err), sizeof(int));
+    if (rc == LIFT_OK && cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess)
+        rc = LIFT_ERR_CUDA;
     if (rc == LIFT_OK && cudaMallocHost(reinterpret_cast<void **>(&b->hout), 3 * sizeof(double) * n) != cudaSuccess) {
         cudaGetLastError();
         b->hout = nullptr;
@@ -1129,7 +1138,10 @@ int lift_batch_energy(lift_batch b, double *out)
         LIFT_CK(lift::launch_energy(b->P[j], b->S[j], b->partial, b->dout + 3 * j, b->stream));
     LIFT_CK(cudaMemcpyAsync(b->hout, b->dout, 3 * sizeof(double) * b->n, cudaMemcpyDeviceToHost,
                             b->stream));
+    int err_word = 0;
+    LIFT_CK(cudaMemcpyAsync(&err_word, b->err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     LIFT_CK(cudaStreamSynchronize(b->stream));
+    if (err_word != 0) return LIFT_ERR_TIMEOUT;
     memcpy(out, b->hout, 3 * sizeof(double) * b->n);
     for (int j = 0; j < 3 * b->n; ++j)
         if (!is_finite(out[j])) return LIFT_ERR_NAN;

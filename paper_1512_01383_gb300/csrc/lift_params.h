@@ -42,6 +42,8 @@ struct LiftParams {
     int blk_off;             // first block of a band launch (0: the whole grid)
     const int *live;         // batch member run by the single-instance kernels:
                              // their blocks return while *live == 0 (null: run)
+    int *err;                // set non-zero by a kernel whose bounded wait for a
+                             // bulk copy gave up (null: not recorded)
 };
 
 // Device state of one problem instance (all float32, see include/lift.h).
@@ -59,8 +61,7 @@ struct InstDesc {
     LiftParams P;
     LiftState S;
     int tile0, ntiles;      // its tiles in the batch's tile list (primal step)
-    int pair0, npairs;      // its units in its dual list: the tile pairs (k >= kPairMinK)
-                            // or the single tiles of the dual step
+    int strip0, nstrips;    // its strips in the batch's strip list (dual step)
 };
 
 // Adjoint buffers of the differentiable solve (adjoint.cu).
@@ -75,9 +76,8 @@ struct AdjState {
 };
 
 constexpr int kStepThreads = 256;
-// The dual step of quadratic pieces on an image takes two tiles per block,
-// with packed projections, from this many intervals per pixel on.
-constexpr int kPairMinK = 4;
+// Threads of a CTA of the batched dual step (strips of 256 / T pixels).
+constexpr int kBatchStripThreads = 256;
 
 // pdhg_step.cu
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
@@ -89,9 +89,14 @@ cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, 
                                cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
 
+// One iteration of the merged batch members: the dual step over all their
+// strips (strip_inst: instance of each strip; stage: shared bytes of the
+// largest strip stage, batch_strip_stage), the primal step over their tiles
+// of `threads` threads.  err: set non-zero if a bounded wait gave up.
 cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *pair_inst, const int *single_inst, const int *live,
-                                   int ntiles, int npairs, int nsingle, cudaStream_t st);
+                                   const int *strip_inst, const int *live, int ntiles,
+                                   int nstrips, int stage, int *err, cudaStream_t st);
+int batch_strip_stage(int k);
 
 // adjoint.cu
 int adjoint_blocks(const LiftParams &P);

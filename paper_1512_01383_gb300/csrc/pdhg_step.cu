@@ -15,21 +15,28 @@
 //     ubar <- 2 u_new - u,  sbar <- 2 s_new - s
 //
 // Memory: label-innermost records, primal float2 {u,s}, extrapolated primal
-// float2 {ubar,sbar}, dual float4 {v,z,px,py}, q one float per pixel.  One
-// thread owns one (pixel, interval) record, so every warp moves one
-// contiguous, fully coalesced run of 8- or 16-byte records.  A block of 256
-// threads holds floor(256/k) whole pixels; the per-pixel sums over the k
-// intervals (the coupling of v, s and q through the operator of Sec. 4) are
-// segmented scans: warp shuffles inside each warp, one shared-memory carry
-// for the pixels that straddle a warp boundary.  Halo values (ubar at x+1
-// and y+1 in the dual step, p at x-1 and y-1 in the primal step) are re-read
-// from L1/L2; the algorithmic DRAM traffic is (20k + 3) floats per pixel and
-// iteration (+ f).  On a volume (D > 1, the d = 3 grid of Sec. 4) p_i has a
-// third component, kept in its own [N][k] float array pz, and the
-// differences add the next / previous slice: (23k + 3) floats per voxel.
+// float2 {ubar,sbar}, dual float4 {v,z,px,py}, q one float per pixel.
+//
+// The dual step of an image (dual_strip_kernel) stages strips of consecutive
+// pixels in shared memory by bulk copies and lets T threads walk each pixel's
+// intervals (see the comment above that kernel).  The primal step, and the
+// dual step of a volume, give one thread one (pixel, interval) record, so
+// every warp moves one contiguous, fully coalesced run of 8- or 16-byte
+// records; a block of 256 threads holds floor(256/k) whole pixels, and the
+// per-pixel sums over the k intervals (the coupling of v, s and q through the
+// operator of Sec. 4) are segmented scans: warp shuffles inside each warp, one
+// shared-memory carry for the pixels that straddle a warp boundary.  Halo
+// values (p at x-1 and y-1 in the primal step) are re-read from L1/L2.  The
+// algorithmic DRAM traffic is (20k + 3) floats per pixel and iteration (+ f).
+// On a volume (D > 1, the d = 3 grid of Sec. 4) p_i has a third component,
+// kept in its own [N][k] float array pz, and the differences add the next /
+// previous slice: (23k + 3) floats per voxel.
+#include "lift_bulk.cuh"
 #include "lift_device.cuh"
 #include "lift_params.h"
 #include "lift_tile.cuh"
+
+#include <algorithm>
 
 namespace lift {
 
@@ -148,134 +155,6 @@ __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__r
     y[o] = make_float4(v, z, px, py);
 }
 
-// Two consecutive tiles (2 pair, 2 pair + 1) of a quadratic-type problem in
-// one block, each thread owning one record of each.  The epigraph projection
-// is the only divergent part of the step: after the first iterations only a
-// few records per warp leave the epigraph (about 2 of 32 per tile on the
-// 512^2, L = 20 denoising problem, yet nearly every warp holds some).  The
-// records below the graph of both tiles are packed into one pass of the warp
-// through a per-warp queue in shared memory (no block barrier), so a warp runs
-// the projection once for two tiles instead of once per tile.  Each record's
-// arithmetic is that of dual_tile.
-template <int THREADS>
-struct PairSmem {
-    float2 in[THREADS];
-    float2 last[THREADS / 32];
-    float4 queue[THREADS / 32][64];
-};
-
-// EARLY: q and f are loaded with the records, before the scan's barrier,
-// so their latency overlaps it (the single-instance kernel: 61.4 -> 57.4 us
-// at 512^2, L = 20, same 48 registers); the batched kernel keeps the late
-// loads, which in it would cost 24 registers.
-template <int THREADS, bool VOL, bool EARLY = false>
-__device__ __forceinline__ void dual_pair(const LiftParams &P, const float2 *__restrict__ xbar,
-                                          float4 *__restrict__ y, float *__restrict__ q,
-                                          float *__restrict__ pz, int pair, PairSmem<THREADS> &sm)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int lp, i;
-    split_thread(P, tid, lp, i);
-    int pix[2]; bool act[2]; size_t o[2]; float2 xb[2]; float4 d[2];
-    float qo[2], fv[2];   // EARLY: q (interval 0) and f of the record's pixel
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        pix[u] = (2 * pair + u) * P.ppb + lp;
-        act[u] = lp < P.ppb && pix[u] < P.N;
-        o[u] = static_cast<size_t>(pix[u]) * P.k + i;
-        xb[u] = make_float2(0.f, 0.f);
-        d[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        qo[u] = fv[u] = 0.f;
-        if (act[u]) {
-            xb[u] = xbar[o[u]];
-            d[u] = y[o[u]];
-            if (EARLY) {
-                if (i == 0) qo[u] = q[pix[u]];
-                fv[u] = __ldg(P.f + pix[u]);
-            }
-        }
-    }
-    const SegScan2 sc = block_segmented_scan2(make_float2(xb[0].y, xb[1].y), lp * P.k, P.k, tid,
-                                              act[0], sm.in, sm.last);
-    const float4 ic = __ldg(P.icst + (lp < P.ppb ? i : 0));  // {gamma_i, tau_s, sigma_vz, lambda*Delta}
-    const float4 stp = __ldg(P.steps);                        // {tau_u, sigma_q, sigma_p, 0}
-    float px[2], py[2], y0[2], h0[2];
-    bool below[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        px[u] = py[u] = y0[u] = h0[u] = 0.0f;
-        below[u] = false;
-        if (!act[u]) continue;
-        const int row = pixel_row(P, pix[u]);
-        const int col = pix[u] - row * P.W;
-        const int yy = VOL ? row_in_slice(P, row) : row;
-
-        // TV dual: forward differences (Neumann), ascent, ball (or box) projection
-        const float gx = col + 1 < P.W ? xbar[o[u] + P.k].x - xb[u].x : 0.0f;
-        const float gy = yy + 1 < P.H ? xbar[o[u] + static_cast<size_t>(P.W) * P.k].x - xb[u].x
-                                      : 0.0f;
-        px[u] = d[u].z + stp.z * gx;
-        py[u] = d[u].w + stp.z * gy;
-        float pzv = 0.0f;
-        if (VOL) {
-            const float gz = pix[u] < P.N - P.HW
-                                 ? xbar[o[u] + static_cast<size_t>(P.HW) * P.k].x - xb[u].x : 0.0f;
-            pzv = pz[o[u]] + stp.z * gz;
-        }
-        if (P.aniso) {
-            px[u] = fminf(fmaxf(px[u], -ic.w), ic.w);
-            py[u] = fminf(fmaxf(py[u], -ic.w), ic.w);
-            if (VOL) pzv = fminf(fmaxf(pzv, -ic.w), ic.w);
-        } else {
-            const float n2 = px[u] * px[u] + py[u] * py[u] + (VOL ? pzv * pzv : 0.0f);
-            if (n2 > ic.w * ic.w) {
-                const float sc2 = ic.w * rsqrtf(n2);
-                px[u] *= sc2;
-                py[u] *= sc2;
-                if (VOL) pzv *= sc2;
-            }
-        }
-        if (VOL) pz[o[u]] = pzv;
-
-        // data duals: sum of sbar over the pixel's later intervals = total - inclusive
-        const float total = u == 0 ? sc.total.x : sc.total.y;
-        const float tail = total - (u == 0 ? sc.incl.x : sc.incl.y);
-        const float v = d[u].x + ic.z * (xb[u].x + P.delta * tail - ic.x * xb[u].y);
-        const float z = d[u].y + ic.z * xb[u].y;
-        if (i == 0) q[pix[u]] = (EARLY ? qo[u] : q[pix[u]]) - stp.y * (1.0f + P.delta * total);
-        y0[u] = v * P.inv_delta;
-        h0[u] = z * P.inv_delta;
-        // the test of piece_in_epigraph<0>, with f already loaded when EARLY
-        below[u] = EARLY ? !(h0[u] >= quad_conj_direct(P, fv[u], ic.x, ic.x + P.delta, y0[u]))
-                         : !piece_in_epigraph<0>(P, pix[u], i, ic.x, y0[u], h0[u]);
-    }
-
-    // queue slots: tile 0's records below the graph, then tile 1's (at most 64)
-    const unsigned m0 = __ballot_sync(0xffffffffu, below[0]);
-    const unsigned m1 = __ballot_sync(0xffffffffu, below[1]);
-    const int n0 = __popc(m0), n = n0 + __popc(m1);
-    const unsigned lt = (1u << lane) - 1u;
-    const int e0 = __popc(m0 & lt), e1 = n0 + __popc(m1 & lt);
-    float4 *qw = sm.queue[warp];
-    if (below[0]) qw[e0] = make_float4(y0[0], h0[0], __int_as_float(pix[0]), __int_as_float(i));
-    if (below[1]) qw[e1] = make_float4(y0[1], h0[1], __int_as_float(pix[1]), __int_as_float(i));
-    __syncwarp();
-    // (v, z) onto Delta * epi(rho_i^*), packed
-    for (int j = lane; j < n; j += 32) {
-        const float4 e = qw[j];
-        const int qp = __float_as_int(e.z), qi = __float_as_int(e.w);
-        float yo, ho;
-        piece_project_below<0>(P, qp, qi, __ldg(P.icst + qi).x, e.x, e.y, yo, ho);
-        qw[j] = make_float4(yo, ho, e.z, e.w);
-    }
-    __syncwarp();
-    if (below[0]) { const float4 r = qw[e0]; y0[0] = r.x; h0[0] = r.y; }
-    if (below[1]) { const float4 r = qw[e1]; y0[1] = r.x; h0[1] = r.y; }
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-        if (act[u]) y[o[u]] = make_float4(P.delta * y0[u], P.delta * h0[u], px[u], py[u]);
-}
-
 template <int THREADS>
 __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restrict__ x,
                                             float2 *__restrict__ xbar,
@@ -319,10 +198,8 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
 }
 
-// LIVE: a batch member, whose blocks return while its live flag is 0.
-// One tile per block: sampled costs (their projection walks the hull's kinks
-// and packing costs more registers than it saves), volumes, and quadratic
-// pieces with k < kPairMinK (few records per pixel, little to pack).
+// The dual step of a volume: one tile per block.  LIVE: a batch member,
+// whose blocks return while its live flag is 0.
 template <int KIND, bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
@@ -334,16 +211,310 @@ dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__
     dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x + P.blk_off, s_in, s_last, pz);
 }
 
-// Quadratic pieces on an image with k >= kPairMinK: two tiles per block with
-// the projections packed (dual_pair).
-template <bool LIVE>
-__global__ void __launch_bounds__(kStepThreads)
-dual_pair_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
-                 float *__restrict__ q)
+// ---------------------------------------------------------------------------
+// Dual step of an image in strips.
+//
+// The pixels are cut into strips of `spp` consecutive pixels, one per CTA.
+// One thread stages by bulk (TMA) copies into shared memory the strip's dual
+// records y, its extrapolated primal records xbar together with those of the
+// pixel after the strip (the x+1 neighbour of its last pixel), and the xbar
+// records of the strip one row below (the y+1 neighbours); the finished y goes
+// back by one bulk store.  Several CTAs per SM overlap one another's copies.
+//
+// T threads share a pixel: thread j of a pixel owns the consecutive intervals
+// [j c, (j+1) c), c = ceil(k/T), and walks them from the last to the first,
+// so the suffix sum sum_{l>i} sbar_l that the v-update needs is a running sum
+// in a register, started from the sums of the later threads' intervals (T-1
+// shuffles; no scan over the block).  Records that leave the epigraph of
+// rho_i^* (a few per cent after the first iterations) are queued per warp;
+// whenever 32 are pending the warp projects them together, one per lane, and
+// what is left at the end of the strip (fewer than 32 per warp) is pooled
+// over the CTA and projected in as few warp passes as it fills, so the
+// divergent projection runs on (nearly) full warps.  The arithmetic of a
+// record is that of dual_tile; only the order of the sum over sbar differs.
+// T depends on k alone, and single problems and batches run one kernel, so a
+// problem gets the same result, bit for bit, whatever the strip length, band
+// cut or batch it runs in.
+// ---------------------------------------------------------------------------
+
+// log2 of the threads per pixel for k intervals.
+__host__ __device__ inline int strip_tshift(int k)
 {
-    __shared__ PairSmem<kStepThreads> sm;
-    if (LIVE && *P.live == 0) return;
-    dual_pair<kStepThreads, false, true>(P, xbar, y, q, nullptr, blockIdx.x + P.blk_off, sm);
+    return k >= 12 ? 2 : (k >= 6 ? 1 : 0);
+}
+
+// Shared memory of a CTA for strips of `spp` pixels with k records each, run
+// by `threads` threads: y, then xbar of the strip and the next pixel (one
+// float2 of slack in front for a first record that sits 8 bytes past a
+// 16-byte boundary, one behind), then xbar of the row below (same slack), then
+// one 64-entry projection ring per warp and the CTA's pool of left-over
+// entries (32 per warp).  `stage` (the three record arrays) is rounded to 128
+// bytes.
+struct StripSmem {
+    int x_off, d_off, stage, ring_off, pool_off, bytes;
+};
+
+__host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
+{
+    StripSmem L;
+    int o = spp * k * 16;
+    L.x_off = o;
+    o += ((spp + 1) * k + 2) * 8;
+    o = (o + 15) & ~15;
+    L.d_off = o;
+    o += (spp * k + 2) * 8;
+    L.stage = (o + 127) & ~127;
+    L.ring_off = L.stage;
+    L.pool_off = L.ring_off + (threads / 32) * 64 * 16;
+    L.bytes = L.pool_off + (threads / 32) * 32 * 16;
+    return L;
+}
+
+// Records [a, e) of xbar into shared memory, dst[r - a] = record r.  The
+// 16-byte aligned middle part moves by one bulk copy: dst starts 8 bytes past
+// a 16-byte boundary exactly when record a does in global memory, so aligned
+// records land on aligned shared addresses.  A first record that sits 8 bytes
+// past a boundary and a last record that starts on one (an 8-byte tail) are
+// plain loads.
+struct XRange {
+    int a, e, s, e2;   // range, and its bulk part [s, e2) (empty if e2 <= s)
+    int ph;            // 1: record a sits 8 bytes past a 16-byte boundary
+};
+
+__device__ __forceinline__ XRange x_range(const float2 *xbar, int a, int e)
+{
+    XRange R;
+    R.a = a;
+    R.e = e;
+    R.ph = static_cast<int>((reinterpret_cast<uintptr_t>(xbar + a) >> 3) & 1);
+    R.s = a + R.ph;
+    R.e2 = e - static_cast<int>((reinterpret_cast<uintptr_t>(xbar + e) >> 3) & 1);
+    return R;
+}
+
+__device__ __forceinline__ void x_ragged(const XRange &R, const float2 *__restrict__ xbar,
+                                         float2 *dst)
+{
+    const int s_end = R.s < R.e ? R.s : R.e;
+    for (int r = R.a; r < s_end; ++r) dst[r - R.a] = xbar[r];
+    int b = R.e2 > R.s ? R.e2 : R.s;
+    if (b < R.a) b = R.a;
+    for (int r = b; r < R.e; ++r) dst[r - R.a] = xbar[r];
+}
+
+// Projection of one queued record onto Delta * epi(rho_i^*), written back into
+// the staged y.  e = {y0, h0, record index in the strip, pixel}.  Not inlined:
+// every record below the graph goes through this one compiled body, whichever
+// warp pass (or kernel) handles it, so its result does not depend on how the
+// records fall into passes.  Pp: the parameters, in shared memory.
+template <int KIND>
+__device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, int pix0, float4 e)
+{
+    const LiftParams &P = *Pp;
+    const int r = __float_as_int(e.z), pp = __float_as_int(e.w);
+    const int i = r - (pp - pix0) * P.k;
+    float yo, ho;
+    piece_project_below<KIND>(P, pp, i, __ldg(P.icst + i).x, e.x, e.y, yo, ho);
+    reinterpret_cast<float2 *>(sY + r)[0] = make_float2(P.delta * yo, P.delta * ho);
+}
+
+// One strip per CTA, of a single problem (D == nullptr: the parameters P1 and
+// state pointers given, the pixels [p0, p1) in strips of blockDim.x / T) or of
+// a batch (strip blockIdx.x belongs to instance strip_inst[blockIdx.x], whose
+// descriptor is D[...]; strips of instances whose live flag is 0 return).
+template <int KIND>
+__global__ void __launch_bounds__(256)
+dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 *__restrict__ y1,
+                  float *__restrict__ q1, int p0, int p1, const InstDesc *__restrict__ D,
+                  const int *__restrict__ strip_inst, const int *__restrict__ live, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ LiftParams sP;
+    __shared__ int s_pool;
+    __shared__ __align__(8) uint64_t s_bar;   // completes when the strip's copies land
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the problem's parameters in registers (the loop below reads them
+    // there) and, for the projections, in shared memory
+    LiftParams P;
+    const float2 *xbar;
+    float4 *y;
+    float *q;
+    int s;
+    if (D == nullptr) {
+        if (P1.live && *P1.live == 0) return;
+        P = P1;
+        xbar = xbar1;
+        y = y1;
+        q = q1;
+        s = blockIdx.x;
+    } else {
+        const int inst = strip_inst[blockIdx.x];
+        if (!live[inst]) return;
+        P = D[inst].P;
+        xbar = D[inst].S.xbar;
+        y = D[inst].S.y;
+        q = D[inst].S.q;
+        s = blockIdx.x - D[inst].strip0;
+        p0 = 0;
+        p1 = P.N;
+    }
+    if (tid == 0) {
+        sP = P;
+        s_pool = 0;
+        mbar_init(&s_bar, 1);                 // initialised before any thread waits on it
+    }
+    __syncthreads();
+    const int k = P.k;
+    const int tshift = strip_tshift(k);
+    const int spp = blockDim.x >> tshift;
+    const StripSmem L = strip_smem(spp, k, blockDim.x);
+    float4 *sRing = reinterpret_cast<float4 *>(smem + L.ring_off) + warp * 64;
+    float4 *sPool = reinterpret_cast<float4 *>(smem + L.pool_off);
+    uint64_t *bar = &s_bar;
+
+    // where the strip lies (record indices fit in int: N*k < 2^31; pixels are
+    // clipped to N first)
+    auto clip = [&](long long p) { return static_cast<int>(p < P.N ? p : P.N); };
+    const int pix0 = p0 + s * spp;
+    const int n = min(spp, p1 - pix0);
+    const int ya = pix0 * k;
+    const XRange RX = x_range(xbar, ya, clip(pix0 + n + 1LL) * k);
+    const XRange RD = x_range(xbar, clip(static_cast<long long>(pix0) + P.W) * k,
+                              clip(static_cast<long long>(pix0) + P.W + n) * k);
+    float4 *sY = reinterpret_cast<float4 *>(smem);
+    float2 *sX = reinterpret_cast<float2 *>(smem + L.x_off) + RX.ph;   // sX[r - RX.a]
+    float2 *sD = reinterpret_cast<float2 *>(smem + L.d_off) + RD.ph;   // sD[r - RD.a]
+
+    if (tid == 0) {
+        const uint32_t yb = static_cast<uint32_t>(n) * k * 16;
+        uint32_t tx = yb;
+        if (RX.e2 > RX.s) tx += (RX.e2 - RX.s) * 8;
+        if (RD.e2 > RD.s) tx += (RD.e2 - RD.s) * 8;
+        mbar_arrive_expect_tx(bar, tx);
+        bulk_load(sY, y + ya, yb, bar);
+        if (RX.e2 > RX.s) bulk_load(sX + (RX.s - RX.a), xbar + RX.s, (RX.e2 - RX.s) * 8, bar);
+        if (RD.e2 > RD.s) bulk_load(sD + (RD.s - RD.a), xbar + RD.s, (RD.e2 - RD.s) * 8, bar);
+    } else if (tid == (blockDim.x > 32 ? 32 : 1)) {   // another warp if there is one
+        x_ragged(RX, xbar, sX);
+        x_ragged(RD, xbar, sD);
+    }
+
+    // this thread: pixel t of the strip (pixels fastest within a warp), and
+    // its share j of the pixel's intervals, [lo, lo + c) clipped to k
+    const int ppw = 32 >> tshift;
+    const int t = warp * ppw + (lane & (ppw - 1));
+    const int j = lane >> (5 - tshift);
+    const int T = 1 << tshift;
+    const int c = (k + T - 1) >> tshift;
+    const int lo = j * c;
+    const bool act = t < n;
+    const int pix = pix0 + t;
+    int row = 0, col = 0;
+    float fv = 0.0f, qo = 0.0f;
+    if (act) {                                 // values that need no staging,
+        row = pixel_row(P, pix);               // loaded while the copies fly
+        col = pix - row * P.W;
+        if (KIND != 2) fv = __ldg(P.f + pix);
+        if (j == 0) qo = q[pix];
+    }
+    const bool hasR = act && col + 1 < P.W, hasD = act && row + 1 < P.H;
+    const float4 stp = __ldg(P.steps);         // {tau_u, sigma_q, sigma_p, 0}
+    const unsigned lt = (1u << lane) - 1u;
+    // the copies have landed (and, by the barrier, the plain-loaded records
+    // are visible); if any thread's bounded wait gave up, the CTA records the
+    // error and leaves
+    const bool landed = mbar_wait(bar, 0);
+    if (__syncthreads_or(!landed)) {
+        if (tid == 0 && err) atomicOr(err, 1);
+        return;
+    }
+
+    // sum of sbar over the intervals of the later threads of this pixel
+    float tail = 0.0f;
+    if (tshift > 0) {
+        float own = 0.0f;
+        for (int it = 0; it < c; ++it) {
+            const int i = lo + it;
+            if (act && i < k) own += sX[t * k + i].y;
+        }
+        for (int d = 1; d < T; ++d) {
+            const float o = __shfl_down_sync(0xffffffffu, own, d * ppw);
+            if (j + d < T) tail += o;
+        }
+    }
+
+    int head = 0, cnt = 0;                     // the warp's ring of queued records
+    for (int it = c - 1; it >= 0; --it) {
+        const int i = lo + it;
+        const bool ok = act && i < k;
+        const int r = t * k + i;
+        bool below = false;
+        float y0 = 0.0f, h0 = 0.0f;
+        if (ok) {
+            const float4 ic = __ldg(P.icst + i);   // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+            const float2 xb = sX[r];
+            const float4 d = sY[r];
+            // TV dual: forward differences (Neumann), ascent, ball (or box) projection
+            const float gx = hasR ? sX[r + k].x - xb.x : 0.0f;
+            const float gy = hasD ? sD[r].x - xb.x : 0.0f;
+            float px = d.z + stp.z * gx;
+            float py = d.w + stp.z * gy;
+            if (P.aniso) {
+                px = fminf(fmaxf(px, -ic.w), ic.w);
+                py = fminf(fmaxf(py, -ic.w), ic.w);
+            } else {
+                const float n2 = px * px + py * py;
+                if (n2 > ic.w * ic.w) {
+                    const float sc2 = ic.w * rsqrtf(n2);
+                    px *= sc2;
+                    py *= sc2;
+                }
+            }
+            const float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
+            const float z = d.y + ic.z * xb.y;
+            tail += xb.y;
+            y0 = v * P.inv_delta;
+            h0 = z * P.inv_delta;
+            below = KIND == 2 ? !piece_in_epigraph<2>(P, pix, i, ic.x, y0, h0)
+                              : !(h0 >= quad_conj_direct(P, fv, ic.x, ic.x + P.delta, y0));
+            sY[r] = make_float4(P.delta * y0, P.delta * h0, px, py);
+        }
+        // (v, z) onto Delta * epi(rho_i^*): queue the records below the graph,
+        // a warp pass whenever 32 are pending
+        const unsigned m = __ballot_sync(0xffffffffu, below);
+        if (below)
+            sRing[(head + cnt + __popc(m & lt)) & 63] =
+                make_float4(y0, h0, __int_as_float(r), __int_as_float(pix));
+        cnt += __popc(m);
+        if (cnt >= 32) {
+            __syncwarp();
+            strip_project<KIND == 2 ? 2 : 0>(&sP, sY, pix0, sRing[(head + lane) & 63]);
+            head = (head + 32) & 63;
+            cnt -= 32;
+            __syncwarp();
+        }
+    }
+    // thread 0 of the pixel ends with the sum of sbar over all intervals
+    if (act && j == 0) q[pix] = qo - stp.y * (1.0f + P.delta * tail);
+
+    // the warps' left-overs (fewer than 32 each) into the CTA's pool, then
+    // projected in passes of 32 spread over the warps
+    int base = 0;
+    if (lane == 0 && cnt > 0) base = atomicAdd(&s_pool, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < cnt) sPool[base + lane] = sRing[(head + lane) & 63];
+    __syncthreads();
+    const int pooled = s_pool;
+    for (int e0 = warp * 32; e0 < pooled; e0 += blockDim.x)
+        if (e0 + lane < pooled) strip_project<KIND == 2 ? 2 : 0>(&sP, sY, pix0, sPool[e0 + lane]);
+
+    fence_proxy_async_smem();                  // the records written above ...
+    __syncthreads();
+    if (tid == 0) {                            // ... go back by one bulk store
+        bulk_store(y + ya, sY, static_cast<uint32_t>(n) * k * 16);
+        bulk_store_commit();
+        bulk_wait_read();                      // the shared memory may then go
+    }
 }
 
 // Single-instance primal step: each block takes two consecutive tiles and
@@ -438,39 +609,8 @@ __device__ __forceinline__ void stage_desc(const InstDesc *__restrict__ D, int i
     __syncthreads();
 }
 
-// Batches hold quadratic-type images only.  Instances with k >= kPairMinK
-// take their dual step in tile pairs, the others in single tiles, as their
-// single-instance kernels do; the two kinds of unit have a list and a kernel
-// each (one kernel holding both bodies would compile them differently from
-// the single-instance kernels).  Block b takes unit b - pair0 of instance
-// unit_inst[b].
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-batch_dual_pair_kernel(const InstDesc *__restrict__ D, const int *__restrict__ unit_inst,
-                       const int *__restrict__ live)
-{
-    __shared__ PairSmem<THREADS> sm;
-    __shared__ InstDesc sd;
-    const int inst = unit_inst[blockIdx.x];
-    if (!live[inst]) return;
-    stage_desc(D, inst, &sd);
-    dual_pair<THREADS, false>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, nullptr, blockIdx.x - sd.pair0, sm);
-}
-
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
-batch_dual_tile_kernel(const InstDesc *__restrict__ D, const int *__restrict__ unit_inst,
-                       const int *__restrict__ live)
-{
-    __shared__ float s_in[THREADS];
-    __shared__ float s_last[THREADS / 32];
-    __shared__ InstDesc sd;
-    const int inst = unit_inst[blockIdx.x];
-    if (!live[inst]) return;
-    stage_desc(D, inst, &sd);
-    dual_tile<0, THREADS>(sd.P, sd.S.xbar, sd.S.y, sd.S.q, blockIdx.x - sd.pair0, s_in, s_last);
-}
-
+// Batches hold quadratic-type images only; their dual step runs in strips
+// (batch_dual_strip_kernel above), their primal step in tiles here.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 batch_primal_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile_inst,
@@ -486,33 +626,51 @@ batch_primal_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile
                          s_last);
 }
 
-template <int THREADS>
-static cudaError_t launch_batch_t(const InstDesc *D, const int *tile_inst, const int *pair_inst,
-                                  const int *single_inst, const int *live, int ntiles, int npairs,
-                                  int nsingle, cudaStream_t st)
+// The dynamic shared-memory limit is a per-device attribute of a kernel: set
+// it to what the strips need before a launch.
+template <int KIND>
+static cudaError_t strip_attr(int bytes)
 {
-    if (npairs > 0) batch_dual_pair_kernel<THREADS><<<npairs, THREADS, 0, st>>>(D, pair_inst, live);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (nsingle > 0)
-        batch_dual_tile_kernel<THREADS><<<nsingle, THREADS, 0, st>>>(D, single_inst, live);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(dual_strip_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                bytes);
+}
+
+template <int THREADS>
+static cudaError_t launch_batch_primal(const InstDesc *D, const int *tile_inst, const int *live,
+                                       int ntiles, cudaStream_t st)
+{
     batch_primal_kernel<THREADS><<<ntiles, THREADS, 0, st>>>(D, tile_inst, live);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *pair_inst, const int *single_inst, const int *live,
-                                   int ntiles, int npairs, int nsingle, cudaStream_t st)
+                                   const int *strip_inst, const int *live, int ntiles,
+                                   int nstrips, int stage, int *err, cudaStream_t st)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (nstrips > 0) {
+        // every strip has kBatchStripThreads threads; stage: the largest staged records
+        const int bytes = stage + (kBatchStripThreads / 32) * 96 * 16;
+        cudaError_t e = strip_attr<0>(bytes);
+        if (e != cudaSuccess) return e;
+        LiftParams none{};
+        dual_strip_kernel<0><<<nstrips, kBatchStripThreads, bytes, st>>>(none, nullptr, nullptr, nullptr,
+                                                                        0, 0, D, strip_inst, live, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     switch (threads) {
-    case 128: return launch_batch_t<128>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
-    case 256: return launch_batch_t<256>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
-    case 512: return launch_batch_t<512>(D, tile_inst, pair_inst, single_inst, live, ntiles, npairs, nsingle, st);
+    case 128: return launch_batch_primal<128>(D, tile_inst, live, ntiles, st);
+    case 256: return launch_batch_primal<256>(D, tile_inst, live, ntiles, st);
+    case 512: return launch_batch_primal<512>(D, tile_inst, live, ntiles, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int batch_strip_stage(int k)
+{
+    return strip_smem(kBatchStripThreads >> strip_tshift(k), k, kBatchStripThreads).stage;
 }
 
 static inline int step_blocks(const LiftParams &P)
@@ -520,37 +678,49 @@ static inline int step_blocks(const LiftParams &P)
     return (P.N + P.ppb - 1) / P.ppb;
 }
 
-// Which dual kernel a problem uses, and its unit (tiles per block).
-static inline bool dual_in_pairs(const LiftParams &P)
+// Pixels per strip for k records per pixel on a single problem: 256 / T
+// threads' worth, fewer (down to 32) while the staged records exceed 40 KB,
+// so that four CTAs fit on an SM.
+static int strip_spp(int k)
 {
-    return P.kind != 2 && P.D == 1 && P.k >= kPairMinK;
+    int spp = 256 >> strip_tshift(k);
+    while (spp > 32 && strip_smem(spp, k, spp << strip_tshift(k)).stage > 40 * 1024) spp -= 32;
+    return spp;
 }
 
-// Dual half-step on the tiles [t0, t1).
+template <int KIND>
+static cudaError_t launch_strips(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                 cudaStream_t st)
+{
+    const int spp = strip_spp(P.k);
+    const int nstrips = (p1 - p0 + spp - 1) / spp;
+    if (nstrips <= 0) return cudaSuccess;
+    const int threads = spp << strip_tshift(P.k);
+    const int bytes = strip_smem(spp, P.k, threads).bytes;
+    const cudaError_t e = strip_attr<KIND>(bytes);
+    if (e != cudaSuccess) return e;
+    dual_strip_kernel<KIND><<<nstrips, threads, bytes, st>>>(P, S.xbar, S.y, S.q, p0, p1, nullptr,
+                                                            nullptr, nullptr, P.err);
+    return cudaGetLastError();
+}
+
+// Dual half-step on the tiles [t0, t1): images in strips (the pixels of those
+// tiles), volumes in tiles.
 cudaError_t launch_dual_band(const LiftParams &P0, const LiftState &S, int t0, int t1,
                              cudaStream_t st)
 {
     LiftParams P = P0;
-    const bool vol = P.D > 1, live = P.live != nullptr;
-    if (dual_in_pairs(P)) {
-        // volumes never belong to a batch, so VOL and LIVE do not meet
-        P.blk_off = t0 / 2;
-        const int nb = (t1 - t0 + 1) / 2;
-        if (live) dual_pair_kernel<true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
-        else dual_pair_kernel<false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q);
-        return cudaGetLastError();
+    if (P.D == 1) {
+        const int p0 = t0 * P.ppb;
+        const int p1 = static_cast<int>(std::min<long long>(static_cast<long long>(t1) * P.ppb, P.N));
+        return P.kind == 2 ? launch_strips<2>(P, S, p0, p1, st) : launch_strips<0>(P, S, p0, p1, st);
     }
     P.blk_off = t0;
     const int nb = t1 - t0;
-    if (P.kind == 2) {
-        if (vol) dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-        else if (live) dual_step_kernel<2, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
-        else dual_step_kernel<2, false, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
-    } else {
-        if (vol) dual_step_kernel<0, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-        else if (live) dual_step_kernel<0, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
-        else dual_step_kernel<0, false, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr);
-    }
+    if (P.kind == 2)
+        dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
+    else
+        dual_step_kernel<0, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 
 LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED, LIFT_PERIODIC_QUAD = 0, 1, 2, 3
 LIFT_OK, LIFT_ERR_SPEC, LIFT_ERR_OOM, LIFT_ERR_CUDA = 0, 1, 2, 3
-LIFT_ERR_NAN, LIFT_ERR_NOT_CONVERGED, LIFT_ERR_ARG = 4, 5, 6
+LIFT_ERR_NAN, LIFT_ERR_NOT_CONVERGED, LIFT_ERR_ARG, LIFT_ERR_TIMEOUT = 4, 5, 6, 7
 LIFT_MAX_K = 64
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblift_gb300.so")
