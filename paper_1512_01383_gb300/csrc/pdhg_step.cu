@@ -265,8 +265,8 @@ __host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
     o += (spp * k + 2) * 8;
     L.stage = (o + 127) & ~127;
     L.ring_off = L.stage;
-    L.pool_off = L.ring_off + (threads / 32) * 64 * 16;
-    L.bytes = L.pool_off + (threads / 32) * 32 * 16;
+    L.pool_off = L.ring_off + (threads / 32) * 64 * 8;
+    L.bytes = L.pool_off + (threads / 32) * 32 * 8;
     return L;
 }
 
@@ -303,19 +303,163 @@ __device__ __forceinline__ void x_ragged(const XRange &R, const float2 *__restri
 }
 
 // Projection of one queued record onto Delta * epi(rho_i^*), written back into
-// the staged y.  e = {y0, h0, record index in the strip, pixel}.  Not inlined:
-// every record below the graph goes through this one compiled body, whichever
-// warp pass (or kernel) handles it, so its result does not depend on how the
+// the staged y.  e = {record index in the strip, pixel}; the record holds the
+// unscaled point (y0, h0) = (v, z) / Delta until then.  Not inlined: every
+// record below the graph goes through this one compiled body, whichever warp
+// pass (or kernel) handles it, so its result does not depend on how the
 // records fall into passes.  Pp: the parameters, in shared memory.
 template <int KIND>
-__device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, int pix0, float4 e)
+__device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, int pix0, int2 e)
 {
     const LiftParams &P = *Pp;
-    const int r = __float_as_int(e.z), pp = __float_as_int(e.w);
+    const int r = e.x, pp = e.y;
     const int i = r - (pp - pix0) * P.k;
+    float2 *rec = reinterpret_cast<float2 *>(sY + r);
+    const float2 p0 = rec[0];
     float yo, ho;
-    piece_project_below<KIND>(P, pp, i, __ldg(P.icst + i).x, e.x, e.y, yo, ho);
-    reinterpret_cast<float2 *>(sY + r)[0] = make_float2(P.delta * yo, P.delta * ho);
+    piece_project_below<KIND>(P, pp, i, __ldg(P.icst + i).x, p0.x, p0.y, yo, ho);
+    rec[0] = make_float2(P.delta * yo, P.delta * ho);
+}
+
+// The dual update of one staged record r (interval i of pixel pix) from its
+// xbar record xb and tail = sum of sbar over the pixel's later intervals:
+// TV dual ascent and ball (or box) projection of p_i; ascent of (v_i, z_i).
+// Writes the record back and returns whether (v, z)/Delta lies below the
+// graph of rho_i^* (then the record keeps the unscaled point for the
+// projection; else it holds the final Delta (y0, h0)).
+template <int KIND>
+__device__ __forceinline__ bool strip_record(const LiftParams &P, float4 *sY, const float2 *sX,
+                                             const float2 *sD, int r, int i, int pix, float fv,
+                                             float2 xb, bool hasR, bool hasD, float sigma_p,
+                                             float tail)
+{
+    const int k = P.k;
+    const float4 ic = __ldg(P.icst + i);       // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+    const float4 d = sY[r];
+    // TV dual: forward differences (Neumann), ascent, ball (or box) projection
+    const float gx = hasR ? sX[r + k].x - xb.x : 0.0f;
+    const float gy = hasD ? sD[r].x - xb.x : 0.0f;
+    float px = d.z + sigma_p * gx;
+    float py = d.w + sigma_p * gy;
+    if (P.aniso) {
+        px = fminf(fmaxf(px, -ic.w), ic.w);
+        py = fminf(fmaxf(py, -ic.w), ic.w);
+    } else {
+        const float n2 = px * px + py * py;
+        if (n2 > ic.w * ic.w) {
+            const float sc2 = ic.w * rsqrtf(n2);
+            px *= sc2;
+            py *= sc2;
+        }
+    }
+    const float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
+    const float z = d.y + ic.z * xb.y;
+    const float y0 = v * P.inv_delta, h0 = z * P.inv_delta;
+    const bool below = KIND == 2 ? !piece_in_epigraph<2>(P, pix, i, ic.x, y0, h0)
+                                 : !(h0 >= quad_conj_direct(P, fv, ic.x, ic.x + P.delta, y0));
+    sY[r] = below ? make_float4(y0, h0, px, py)
+                  : make_float4(P.delta * y0, P.delta * h0, px, py);
+    return below;
+}
+
+// A warp's ring of queued records: entries [head, head + cnt) (mod 64).
+struct StripRing {
+    int2 *e;
+    int head, cnt;
+};
+
+// Queue this lane's record (if below) and run a warp pass of the projection
+// whenever 32 are pending.
+template <int KIND>
+__device__ __forceinline__ void strip_queue(StripRing &R, bool below, int r, int pix, int lane,
+                                            const LiftParams *sP, float4 *sY, int pix0)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, below);
+    if (below) R.e[(R.head + R.cnt + __popc(m & ((1u << lane) - 1u))) & 63] = make_int2(r, pix);
+    R.cnt += __popc(m);
+    if (R.cnt >= 32) {
+        __syncwarp();
+        strip_project<KIND>(sP, sY, pix0, R.e[(R.head + lane) & 63]);
+        R.head = (R.head + 32) & 63;
+        R.cnt -= 32;
+        __syncwarp();
+    }
+}
+
+// This thread's share of a pixel: the C intervals [lo, lo + C) clipped to k
+// (C a compile-time length, so the records' loads and arithmetic interleave).
+// Returns the sum of sbar over the pixel's intervals from lo on (plus the
+// later threads' sums, which it adds first).
+template <int KIND, int C>
+__device__ __forceinline__ float strip_chunk(const LiftParams &P, const LiftParams *sP, float4 *sY,
+                                             const float2 *sX, const float2 *sD, StripRing &R,
+                                             int pix0, int t, int lo, int tshift, bool act,
+                                             bool hasR, bool hasD, float fv, float sigma_p,
+                                             int lane)
+{
+    const int k = P.k, pix = pix0 + t;
+    float2 xb[C];
+    float own = 0.0f;
+#pragma unroll
+    for (int it = 0; it < C; ++it) {
+        const bool ok = act && lo + it < k;
+        xb[it] = ok ? sX[t * k + lo + it] : make_float2(0.0f, 0.0f);
+        own += xb[it].y;
+    }
+    // sum of sbar over the intervals of the later threads of this pixel
+    float tail = 0.0f;
+    const int ppw = 32 >> tshift, T = 1 << tshift, j = lane >> (5 - tshift);
+    for (int d = 1; d < T; ++d) {
+        const float o = __shfl_down_sync(0xffffffffu, own, d * ppw);
+        if (j + d < T) tail += o;
+    }
+    bool below[C];
+#pragma unroll
+    for (int it = C - 1; it >= 0; --it) {
+        const int i = lo + it;
+        below[it] = false;
+        if (act && i < k)
+            below[it] = strip_record<KIND>(P, sY, sX, sD, t * k + i, i, pix, fv, xb[it], hasR,
+                                           hasD, sigma_p, tail);
+        tail += xb[it].y;
+    }
+#pragma unroll
+    for (int it = C - 1; it >= 0; --it)
+        strip_queue<KIND>(R, below[it], t * k + lo + it, pix, lane, sP, sY, pix0);
+    return tail;
+}
+
+// The same for chunks longer than 8 (k > 32 with four threads per pixel), in
+// a loop.
+template <int KIND>
+__device__ __forceinline__ float strip_chunk_any(const LiftParams &P, const LiftParams *sP,
+                                                 float4 *sY, const float2 *sX, const float2 *sD,
+                                                 StripRing &R, int pix0, int t, int lo, int c,
+                                                 int tshift, bool act, bool hasR, bool hasD,
+                                                 float fv, float sigma_p, int lane)
+{
+    const int k = P.k, pix = pix0 + t;
+    float own = 0.0f;
+    for (int it = 0; it < c; ++it)
+        if (act && lo + it < k) own += sX[t * k + lo + it].y;
+    float tail = 0.0f;
+    const int ppw = 32 >> tshift, T = 1 << tshift, j = lane >> (5 - tshift);
+    for (int d = 1; d < T; ++d) {
+        const float o = __shfl_down_sync(0xffffffffu, own, d * ppw);
+        if (j + d < T) tail += o;
+    }
+    for (int it = c - 1; it >= 0; --it) {
+        const int i = lo + it;
+        bool below = false;
+        if (act && i < k) {
+            const float2 xb = sX[t * k + i];
+            below = strip_record<KIND>(P, sY, sX, sD, t * k + i, i, pix, fv, xb, hasR, hasD,
+                                       sigma_p, tail);
+            tail += xb.y;
+        }
+        strip_queue<KIND>(R, below, t * k + i, pix, lane, sP, sY, pix0);
+    }
+    return tail;
 }
 
 // One strip per CTA, of a single problem (D == nullptr: the parameters P1 and
@@ -368,8 +512,8 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     const int tshift = strip_tshift(k);
     const int spp = blockDim.x >> tshift;
     const StripSmem L = strip_smem(spp, k, blockDim.x);
-    float4 *sRing = reinterpret_cast<float4 *>(smem + L.ring_off) + warp * 64;
-    float4 *sPool = reinterpret_cast<float4 *>(smem + L.pool_off);
+    int2 *sRing = reinterpret_cast<int2 *>(smem + L.ring_off) + warp * 64;
+    int2 *sPool = reinterpret_cast<int2 *>(smem + L.pool_off);
     uint64_t *bar = &s_bar;
 
     // where the strip lies (record indices fit in int: N*k < 2^31; pixels are
@@ -419,7 +563,6 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     }
     const bool hasR = act && col + 1 < P.W, hasD = act && row + 1 < P.H;
     const float4 stp = __ldg(P.steps);         // {tau_u, sigma_q, sigma_p, 0}
-    const unsigned lt = (1u << lane) - 1u;
     // the copies have landed (and, by the barrier, the plain-loaded records
     // are visible); if any thread's bounded wait gave up, the CTA records the
     // error and leaves
@@ -429,70 +572,21 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
         return;
     }
 
-    // sum of sbar over the intervals of the later threads of this pixel
-    float tail = 0.0f;
-    if (tshift > 0) {
-        float own = 0.0f;
-        for (int it = 0; it < c; ++it) {
-            const int i = lo + it;
-            if (act && i < k) own += sX[t * k + i].y;
-        }
-        for (int d = 1; d < T; ++d) {
-            const float o = __shfl_down_sync(0xffffffffu, own, d * ppw);
-            if (j + d < T) tail += o;
-        }
-    }
-
-    int head = 0, cnt = 0;                     // the warp's ring of queued records
-    for (int it = c - 1; it >= 0; --it) {
-        const int i = lo + it;
-        const bool ok = act && i < k;
-        const int r = t * k + i;
-        bool below = false;
-        float y0 = 0.0f, h0 = 0.0f;
-        if (ok) {
-            const float4 ic = __ldg(P.icst + i);   // {gamma_i, tau_s, sigma_vz, lambda*Delta}
-            const float2 xb = sX[r];
-            const float4 d = sY[r];
-            // TV dual: forward differences (Neumann), ascent, ball (or box) projection
-            const float gx = hasR ? sX[r + k].x - xb.x : 0.0f;
-            const float gy = hasD ? sD[r].x - xb.x : 0.0f;
-            float px = d.z + stp.z * gx;
-            float py = d.w + stp.z * gy;
-            if (P.aniso) {
-                px = fminf(fmaxf(px, -ic.w), ic.w);
-                py = fminf(fmaxf(py, -ic.w), ic.w);
-            } else {
-                const float n2 = px * px + py * py;
-                if (n2 > ic.w * ic.w) {
-                    const float sc2 = ic.w * rsqrtf(n2);
-                    px *= sc2;
-                    py *= sc2;
-                }
-            }
-            const float v = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
-            const float z = d.y + ic.z * xb.y;
-            tail += xb.y;
-            y0 = v * P.inv_delta;
-            h0 = z * P.inv_delta;
-            below = KIND == 2 ? !piece_in_epigraph<2>(P, pix, i, ic.x, y0, h0)
-                              : !(h0 >= quad_conj_direct(P, fv, ic.x, ic.x + P.delta, y0));
-            sY[r] = make_float4(P.delta * y0, P.delta * h0, px, py);
-        }
-        // (v, z) onto Delta * epi(rho_i^*): queue the records below the graph,
-        // a warp pass whenever 32 are pending
-        const unsigned m = __ballot_sync(0xffffffffu, below);
-        if (below)
-            sRing[(head + cnt + __popc(m & lt)) & 63] =
-                make_float4(y0, h0, __int_as_float(r), __int_as_float(pix));
-        cnt += __popc(m);
-        if (cnt >= 32) {
-            __syncwarp();
-            strip_project<KIND == 2 ? 2 : 0>(&sP, sY, pix0, sRing[(head + lane) & 63]);
-            head = (head + 32) & 63;
-            cnt -= 32;
-            __syncwarp();
-        }
+    StripRing R{sRing, 0, 0};
+    constexpr int PK = KIND == 2 ? 2 : 0;
+    float tail;
+    switch (c) {
+    case 1: tail = strip_chunk<PK, 1>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 2: tail = strip_chunk<PK, 2>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 3: tail = strip_chunk<PK, 3>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 4: tail = strip_chunk<PK, 4>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 5: tail = strip_chunk<PK, 5>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 6: tail = strip_chunk<PK, 6>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 7: tail = strip_chunk<PK, 7>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 8: tail = strip_chunk<PK, 8>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    default:
+        tail = strip_chunk_any<PK>(P, &sP, sY, sX, sD, R, pix0, t, lo, c, tshift, act, hasR, hasD, fv,
+                                   stp.z, lane);
     }
     // thread 0 of the pixel ends with the sum of sbar over all intervals
     if (act && j == 0) q[pix] = qo - stp.y * (1.0f + P.delta * tail);
@@ -500,13 +594,13 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     // the warps' left-overs (fewer than 32 each) into the CTA's pool, then
     // projected in passes of 32 spread over the warps
     int base = 0;
-    if (lane == 0 && cnt > 0) base = atomicAdd(&s_pool, cnt);
+    if (lane == 0 && R.cnt > 0) base = atomicAdd(&s_pool, R.cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (lane < cnt) sPool[base + lane] = sRing[(head + lane) & 63];
+    if (lane < R.cnt) sPool[base + lane] = sRing[(R.head + lane) & 63];
     __syncthreads();
     const int pooled = s_pool;
     for (int e0 = warp * 32; e0 < pooled; e0 += blockDim.x)
-        if (e0 + lane < pooled) strip_project<KIND == 2 ? 2 : 0>(&sP, sY, pix0, sPool[e0 + lane]);
+        if (e0 + lane < pooled) strip_project<PK>(&sP, sY, pix0, sPool[e0 + lane]);
 
     fence_proxy_async_smem();                  // the records written above ...
     __syncthreads();
@@ -651,7 +745,7 @@ cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *ti
     if (ntiles <= 0) return cudaSuccess;
     if (nstrips > 0) {
         // every strip has kBatchStripThreads threads; stage: the largest staged records
-        const int bytes = stage + (kBatchStripThreads / 32) * 96 * 16;
+        const int bytes = stage + (kBatchStripThreads / 32) * 96 * 8;
         cudaError_t e = strip_attr<0>(bytes);
         if (e != cudaSuccess) return e;
         LiftParams none{};
