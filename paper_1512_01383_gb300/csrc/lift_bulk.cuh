@@ -74,6 +74,13 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint
                  : "memory");
 }
 
+// Prefetch `bytes` (a multiple of 16) from a 16-byte aligned global address
+// into L2, with no destination and no completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Order this thread's earlier generic-proxy writes to shared memory (made
 // visible to it by a block barrier) before later bulk copies read it.
 __device__ __forceinline__ void fence_proxy_async_smem()

@@ -260,12 +260,17 @@ __device__ __forceinline__ float periodic_center(float f, float per, float l, fl
     return f + per * floorf((0.5f * (l + r) - f) / per + 0.5f);
 }
 
-__device__ __forceinline__ QPiece make_qpiece(const LiftParams &P, int pix, float l, float r)
+// The piece on [l, r] of a pixel whose data value is f.
+__device__ __forceinline__ QPiece make_qpiece_f(const LiftParams &P, float f, float l, float r)
 {
-    const float f = __ldg(P.f + pix);
     if (P.kind == 3) return make_quad_piece<float>(P.alpha, periodic_center(f, P.nu, l, r), l, r);
     return P.kind == 0 ? make_quad_piece<float>(P.alpha, f, l, r)
                        : make_trunc_piece<float>(P.alpha, P.nu, P.wtrunc, f, l, r);
+}
+
+__device__ __forceinline__ QPiece make_qpiece(const LiftParams &P, int pix, float l, float r)
+{
+    return make_qpiece_f(P, __ldg(P.f + pix), l, r);
 }
 
 // rho_i^*(y) of pixel pix, interval i, for any kind.

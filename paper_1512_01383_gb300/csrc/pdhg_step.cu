@@ -247,11 +247,11 @@ __host__ __device__ inline int strip_tshift(int k)
 // by `threads` threads: y, then xbar of the strip and the next pixel (one
 // float2 of slack in front for a first record that sits 8 bytes past a
 // 16-byte boundary, one behind), then xbar of the row below (same slack), then
-// one 64-entry projection ring per warp and the CTA's pool of left-over
-// entries (32 per warp).  `stage` (the three record arrays) is rounded to 128
-// bytes.
+// the per-interval constants (k float4), one 64-entry projection ring per
+// warp and the CTA's pool of left-over entries (32 per warp).  `stage` (the
+// three record arrays) is rounded to 128 bytes.
 struct StripSmem {
-    int x_off, d_off, stage, ring_off, pool_off, bytes;
+    int x_off, d_off, stage, ic_off, ring_off, pool_off, bytes;
 };
 
 __host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
@@ -264,9 +264,10 @@ __host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
     L.d_off = o;
     o += (spp * k + 2) * 8;
     L.stage = (o + 127) & ~127;
-    L.ring_off = L.stage;
-    L.pool_off = L.ring_off + (threads / 32) * 64 * 8;
-    L.bytes = L.pool_off + (threads / 32) * 32 * 8;
+    L.ic_off = L.stage;
+    L.ring_off = L.ic_off + k * 16;
+    L.pool_off = L.ring_off + (threads / 32) * 64 * 16;
+    L.bytes = L.pool_off + (threads / 32) * 32 * 16;
     return L;
 }
 
@@ -303,21 +304,29 @@ __device__ __forceinline__ void x_ragged(const XRange &R, const float2 *__restri
 }
 
 // Projection of one queued record onto Delta * epi(rho_i^*), written back into
-// the staged y.  e = {record index in the strip, pixel}; the record holds the
-// unscaled point (y0, h0) = (v, z) / Delta until then.  Not inlined: every
-// record below the graph goes through this one compiled body, whichever warp
-// pass (or kernel) handles it, so its result does not depend on how the
+// the staged y.  e = {record index in the strip, pixel, f of the pixel (the
+// quadratic kinds)}; the record holds the unscaled point (y0, h0) = (v, z) /
+// Delta until then; sIC: the staged per-interval constants.  Not inlined:
+// every record below the graph goes through this one compiled body, whichever
+// warp pass (or kernel) handles it, so its result does not depend on how the
 // records fall into passes.  Pp: the parameters, in shared memory.
 template <int KIND>
-__device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, int pix0, int2 e)
+__device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, const float4 *sIC,
+                                           int pix0, int4 e)
 {
     const LiftParams &P = *Pp;
     const int r = e.x, pp = e.y;
     const int i = r - (pp - pix0) * P.k;
     float2 *rec = reinterpret_cast<float2 *>(sY + r);
     const float2 p0 = rec[0];
+    const float l = sIC[i].x;
     float yo, ho;
-    piece_project_below<KIND>(P, pp, i, __ldg(P.icst + i).x, p0.x, p0.y, yo, ho);
+    if (KIND == 2) {
+        piece_project_below<2>(P, pp, i, l, p0.x, p0.y, yo, ho);
+    } else {
+        const QPiece qp = make_qpiece_f(P, __int_as_float(e.z), l, l + P.delta);
+        qpiece_project(qp, p0.x, p0.y, yo, ho);
+    }
     rec[0] = make_float2(P.delta * yo, P.delta * ho);
 }
 
@@ -329,12 +338,12 @@ __device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, int
 // projection; else it holds the final Delta (y0, h0)).
 template <int KIND>
 __device__ __forceinline__ bool strip_record(const LiftParams &P, float4 *sY, const float2 *sX,
-                                             const float2 *sD, int r, int i, int pix, float fv,
-                                             float2 xb, bool hasR, bool hasD, float sigma_p,
-                                             float tail)
+                                             const float2 *sD, const float4 *sIC, int r, int i,
+                                             int pix, float fv, float2 xb, bool hasR, bool hasD,
+                                             float sigma_p, float tail)
 {
     const int k = P.k;
-    const float4 ic = __ldg(P.icst + i);       // {gamma_i, tau_s, sigma_vz, lambda*Delta}
+    const float4 ic = sIC[i];                  // {gamma_i, tau_s, sigma_vz, lambda*Delta}
     const float4 d = sY[r];
     // TV dual: forward differences (Neumann), ascent, ball (or box) projection
     const float gx = hasR ? sX[r + k].x - xb.x : 0.0f;
@@ -362,24 +371,28 @@ __device__ __forceinline__ bool strip_record(const LiftParams &P, float4 *sY, co
     return below;
 }
 
-// A warp's ring of queued records: entries [head, head + cnt) (mod 64).
+// A warp's ring of queued records: entries [head, head + cnt) (mod 64), each
+// {record, pixel, f of the pixel, unused}.
 struct StripRing {
-    int2 *e;
+    int4 *e;
     int head, cnt;
 };
 
 // Queue this lane's record (if below) and run a warp pass of the projection
 // whenever 32 are pending.
 template <int KIND>
-__device__ __forceinline__ void strip_queue(StripRing &R, bool below, int r, int pix, int lane,
-                                            const LiftParams *sP, float4 *sY, int pix0)
+__device__ __forceinline__ void strip_queue(StripRing &R, bool below, int r, int pix, float fv,
+                                            int lane, const LiftParams *sP, float4 *sY,
+                                            const float4 *sIC, int pix0)
 {
     const unsigned m = __ballot_sync(0xffffffffu, below);
-    if (below) R.e[(R.head + R.cnt + __popc(m & ((1u << lane) - 1u))) & 63] = make_int2(r, pix);
+    if (below)
+        R.e[(R.head + R.cnt + __popc(m & ((1u << lane) - 1u))) & 63] =
+            make_int4(r, pix, __float_as_int(fv), 0);
     R.cnt += __popc(m);
     if (R.cnt >= 32) {
         __syncwarp();
-        strip_project<KIND>(sP, sY, pix0, R.e[(R.head + lane) & 63]);
+        strip_project<KIND>(sP, sY, sIC, pix0, R.e[(R.head + lane) & 63]);
         R.head = (R.head + 32) & 63;
         R.cnt -= 32;
         __syncwarp();
@@ -392,7 +405,8 @@ __device__ __forceinline__ void strip_queue(StripRing &R, bool below, int r, int
 // later threads' sums, which it adds first).
 template <int KIND, int C>
 __device__ __forceinline__ float strip_chunk(const LiftParams &P, const LiftParams *sP, float4 *sY,
-                                             const float2 *sX, const float2 *sD, StripRing &R,
+                                             const float2 *sX, const float2 *sD,
+                                             const float4 *sIC, StripRing &R,
                                              int pix0, int t, int lo, int tshift, bool act,
                                              bool hasR, bool hasD, float fv, float sigma_p,
                                              int lane)
@@ -419,13 +433,13 @@ __device__ __forceinline__ float strip_chunk(const LiftParams &P, const LiftPara
         const int i = lo + it;
         below[it] = false;
         if (act && i < k)
-            below[it] = strip_record<KIND>(P, sY, sX, sD, t * k + i, i, pix, fv, xb[it], hasR,
-                                           hasD, sigma_p, tail);
+            below[it] = strip_record<KIND>(P, sY, sX, sD, sIC, t * k + i, i, pix, fv, xb[it],
+                                           hasR, hasD, sigma_p, tail);
         tail += xb[it].y;
     }
 #pragma unroll
     for (int it = C - 1; it >= 0; --it)
-        strip_queue<KIND>(R, below[it], t * k + lo + it, pix, lane, sP, sY, pix0);
+        strip_queue<KIND>(R, below[it], t * k + lo + it, pix, fv, lane, sP, sY, sIC, pix0);
     return tail;
 }
 
@@ -434,7 +448,7 @@ __device__ __forceinline__ float strip_chunk(const LiftParams &P, const LiftPara
 template <int KIND>
 __device__ __forceinline__ float strip_chunk_any(const LiftParams &P, const LiftParams *sP,
                                                  float4 *sY, const float2 *sX, const float2 *sD,
-                                                 StripRing &R, int pix0, int t, int lo, int c,
+                                                 const float4 *sIC, StripRing &R, int pix0, int t, int lo, int c,
                                                  int tshift, bool act, bool hasR, bool hasD,
                                                  float fv, float sigma_p, int lane)
 {
@@ -453,11 +467,11 @@ __device__ __forceinline__ float strip_chunk_any(const LiftParams &P, const Lift
         bool below = false;
         if (act && i < k) {
             const float2 xb = sX[t * k + i];
-            below = strip_record<KIND>(P, sY, sX, sD, t * k + i, i, pix, fv, xb, hasR, hasD,
-                                       sigma_p, tail);
+            below = strip_record<KIND>(P, sY, sX, sD, sIC, t * k + i, i, pix, fv, xb, hasR,
+                                       hasD, sigma_p, tail);
             tail += xb.y;
         }
-        strip_queue<KIND>(R, below, t * k + i, pix, lane, sP, sY, pix0);
+        strip_queue<KIND>(R, below, t * k + i, pix, fv, lane, sP, sY, sIC, pix0);
     }
     return tail;
 }
@@ -467,10 +481,11 @@ __device__ __forceinline__ float strip_chunk_any(const LiftParams &P, const Lift
 // a batch (strip blockIdx.x belongs to instance strip_inst[blockIdx.x], whose
 // descriptor is D[...]; strips of instances whose live flag is 0 return).
 template <int KIND>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 *__restrict__ y1,
                   float *__restrict__ q1, int p0, int p1, const InstDesc *__restrict__ D,
-                  const int *__restrict__ strip_inst, const int *__restrict__ live, int *err)
+                  const int *__restrict__ strip_inst, const int *__restrict__ live, int *err,
+                  int ahead)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ LiftParams sP;
@@ -512,8 +527,9 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     const int tshift = strip_tshift(k);
     const int spp = blockDim.x >> tshift;
     const StripSmem L = strip_smem(spp, k, blockDim.x);
-    int2 *sRing = reinterpret_cast<int2 *>(smem + L.ring_off) + warp * 64;
-    int2 *sPool = reinterpret_cast<int2 *>(smem + L.pool_off);
+    float4 *sIC = reinterpret_cast<float4 *>(smem + L.ic_off);
+    int4 *sRing = reinterpret_cast<int4 *>(smem + L.ring_off) + warp * 64;
+    int4 *sPool = reinterpret_cast<int4 *>(smem + L.pool_off);
     uint64_t *bar = &s_bar;
 
     // where the strip lies (record indices fit in int: N*k < 2^31; pixels are
@@ -531,13 +547,23 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
 
     if (tid == 0) {
         const uint32_t yb = static_cast<uint32_t>(n) * k * 16;
-        uint32_t tx = yb;
+        uint32_t tx = yb + k * 16;
         if (RX.e2 > RX.s) tx += (RX.e2 - RX.s) * 8;
         if (RD.e2 > RD.s) tx += (RD.e2 - RD.s) * 8;
         mbar_arrive_expect_tx(bar, tx);
         bulk_load(sY, y + ya, yb, bar);
         if (RX.e2 > RX.s) bulk_load(sX + (RX.s - RX.a), xbar + RX.s, (RX.e2 - RX.s) * 8, bar);
         if (RD.e2 > RD.s) bulk_load(sD + (RD.s - RD.a), xbar + RD.s, (RD.e2 - RD.s) * 8, bar);
+        bulk_load(sIC, P.icst, k * 16, bar);
+        // the strip that the CTA taking this one's place `ahead` launches
+        // later will stage: its y and xbar into L2 now
+        const int s2 = s + ahead;
+        if (ahead > 0 && p0 + static_cast<long long>(s2) * spp < p1) {
+            const int q0 = p0 + s2 * spp, nq = min(spp, p1 - q0);
+            bulk_prefetch_l2(y + q0 * k, static_cast<uint32_t>(nq) * k * 16);
+            const XRange RQ = x_range(xbar, q0 * k, clip(q0 + nq + 1LL) * k);
+            if (RQ.e2 > RQ.s) bulk_prefetch_l2(xbar + RQ.s, (RQ.e2 - RQ.s) * 8);
+        }
     } else if (tid == (blockDim.x > 32 ? 32 : 1)) {   // another warp if there is one
         x_ragged(RX, xbar, sX);
         x_ragged(RD, xbar, sD);
@@ -576,16 +602,16 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     constexpr int PK = KIND == 2 ? 2 : 0;
     float tail;
     switch (c) {
-    case 1: tail = strip_chunk<PK, 1>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 2: tail = strip_chunk<PK, 2>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 3: tail = strip_chunk<PK, 3>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 4: tail = strip_chunk<PK, 4>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 5: tail = strip_chunk<PK, 5>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 6: tail = strip_chunk<PK, 6>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 7: tail = strip_chunk<PK, 7>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
-    case 8: tail = strip_chunk<PK, 8>(P, &sP, sY, sX, sD, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 1: tail = strip_chunk<PK, 1>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 2: tail = strip_chunk<PK, 2>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 3: tail = strip_chunk<PK, 3>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 4: tail = strip_chunk<PK, 4>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 5: tail = strip_chunk<PK, 5>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 6: tail = strip_chunk<PK, 6>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 7: tail = strip_chunk<PK, 7>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 8: tail = strip_chunk<PK, 8>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
     default:
-        tail = strip_chunk_any<PK>(P, &sP, sY, sX, sD, R, pix0, t, lo, c, tshift, act, hasR, hasD, fv,
+        tail = strip_chunk_any<PK>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, c, tshift, act, hasR, hasD, fv,
                                    stp.z, lane);
     }
     // thread 0 of the pixel ends with the sum of sbar over all intervals
@@ -600,7 +626,7 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     __syncthreads();
     const int pooled = s_pool;
     for (int e0 = warp * 32; e0 < pooled; e0 += blockDim.x)
-        if (e0 + lane < pooled) strip_project<PK>(&sP, sY, pix0, sPool[e0 + lane]);
+        if (e0 + lane < pooled) strip_project<PK>(&sP, sY, sIC, pix0, sPool[e0 + lane]);
 
     fence_proxy_async_smem();                  // the records written above ...
     __syncthreads();
@@ -745,12 +771,12 @@ cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *ti
     if (ntiles <= 0) return cudaSuccess;
     if (nstrips > 0) {
         // every strip has kBatchStripThreads threads; stage: the largest staged records
-        const int bytes = stage + (kBatchStripThreads / 32) * 96 * 8;
+        const int bytes = stage + 64 * 16 + (kBatchStripThreads / 32) * 96 * 16;
         cudaError_t e = strip_attr<0>(bytes);
         if (e != cudaSuccess) return e;
         LiftParams none{};
         dual_strip_kernel<0><<<nstrips, kBatchStripThreads, bytes, st>>>(none, nullptr, nullptr, nullptr,
-                                                                        0, 0, D, strip_inst, live, err);
+                                                                        0, 0, D, strip_inst, live, err, 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -791,10 +817,18 @@ static cudaError_t launch_strips(const LiftParams &P, const LiftState &S, int p0
     if (nstrips <= 0) return cudaSuccess;
     const int threads = spp << strip_tshift(P.k);
     const int bytes = strip_smem(spp, P.k, threads).bytes;
-    const cudaError_t e = strip_attr<KIND>(bytes);
+    cudaError_t e = strip_attr<KIND>(bytes);
+    if (e != cudaSuccess) return e;
+    // CTAs resident at once: a CTA prefetches the strip of the CTA that will
+    // take its place
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dual_strip_kernel<KIND>, threads, bytes);
     if (e != cudaSuccess) return e;
     dual_strip_kernel<KIND><<<nstrips, threads, bytes, st>>>(P, S.xbar, S.y, S.q, p0, p1, nullptr,
-                                                            nullptr, nullptr, P.err);
+                                                            nullptr, nullptr, P.err, per_sm * sms);
     return cudaGetLastError();
 }
 
