@@ -64,9 +64,9 @@ extern "C" {
  *                  distance to the wrapped data f(x), approximated on each
  *                  Gamma_i by the parabola alpha/2 (t - c_i)^2 of the
  *                  periodic copy c_i = f + nu m (m integer, nu = the period,
- *                  e.g. 2 pi) nearest to the interval's midpoint; at a
- *                  label (within 1e-4 of an interval width) rho is the
- *                  smaller of the two adjacent pieces
+ *                  e.g. 2 pi) nearest to the interval's midpoint; the
+ *                  nonconvex energy E_nc evaluates rho itself, alpha/2
+ *                  times the squared circular distance of t to f
  * Each interval Gamma_i = [gamma_i, gamma_{i+1}] sees only the convex
  * envelope rho_i^** of rho restricted to it (Prop. 1).  For the two
  * quadratic kinds the envelope is linear-quadratic-linear and is derived in

@@ -51,9 +51,11 @@ typedef struct {
     int kind;              /* ORC_QUAD: rho = alpha/2 (t-f)^2
                               ORC_TRUNC: rho = min(alpha (t-f)^2, nu)
                               ORC_PL: rho = PL interpolant of sampled costs
-                              ORC_PERIODIC: on Gamma_i, alpha/2 (t-c_i)^2,
+                              ORC_PERIODIC: rho = alpha/2 times the squared
+                              circular distance to f (period nu), seen by
+                              the relaxation on Gamma_i as alpha/2 (t-c_i)^2,
                               c_i the copy f + nu*m nearest the interval's
-                              midpoint (nu = period; Sec. 5.5) */
+                              midpoint (Sec. 5.5) */
     int H, W, L;           /* image size, number of labels (k = L-1)      */
     double gmin, gmax;     /* label range Gamma = [gmin, gmax], equidistant */
     double lam;            /* TV weight lambda                             */
@@ -150,26 +152,18 @@ static double periodic_piece(const orc_problem *P, int pix, int i, double t)
     return 0.5 * P->alpha * d * d;
 }
 
-/* rho(t): the piece of the interval that contains t; at a label (within
-   1e-4 of an interval width, which covers single-precision rounding of a
-   value that sits on a label) the smaller of the two adjacent pieces. */
+/* rho(t) itself (Sec. 5.5): alpha/2 times the squared circular distance of t
+   to the data, min over integers m of (t - f - nu m)^2.  The nearest copy is
+   f + nu m with m = floor((t - f)/nu) or m + 1, so the minimum over those two
+   is the minimum over all m.  Only the nonconvex energy E_nc reads this; the
+   relaxation sees the per-interval parabolas above. */
 static double periodic_rho(const orc_problem *P, int pix, double t)
 {
-    int k = P->L - 1;
-    double x = (t - P->gmin) / ((P->gmax - P->gmin) / (double)k);
-    int i0 = (int)floor(x);
-    if (i0 < 0) i0 = 0;
-    if (i0 > k - 1) i0 = k - 1;
-    double best = periodic_piece(P, pix, i0, t);
-    if (x - i0 < 1e-4 && i0 > 0) {
-        double b = periodic_piece(P, pix, i0 - 1, t);
-        if (b < best) best = b;
-    }
-    if ((double)(i0 + 1) - x < 1e-4 && i0 + 1 < k) {
-        double b = periodic_piece(P, pix, i0 + 1, t);
-        if (b < best) best = b;
-    }
-    return best;
+    double f = P->f[pix], per = P->nu;
+    double m = floor((t - f) / per);
+    double d1 = t - f - per * m, d2 = t - f - per * (m + 1.0);
+    double d = fabs(d1) < fabs(d2) ? d1 : d2;
+    return 0.5 * P->alpha * d * d;
 }
 
 double orc_rho(const orc_problem *P, int pix, double t)

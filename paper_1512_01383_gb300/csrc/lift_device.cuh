@@ -154,9 +154,9 @@ __device__ __forceinline__ float cubic_outer_root(float p, float Q)
 // On a ray the projection is onto a line; on the parabola, with
 // w = c + y/a, G'(y) = (a/2)(w^3 + p w + q) with p = 2 - c^2 - 2 h0/a,
 // q = -2 (c + y0/a), and the projection is its outermost root (the side of
-// -q), polished by one Newton step.  (For a dual-number T the closed-form
-// root enters as a constant; the Newton step then carries the derivative of
-// the root by the implicit-function theorem.)
+// -q), polished by one Newton step on d = w - c.  (For a dual-number T the
+// closed-form root enters as a constant; the Newton step then carries the
+// derivative of the root by the implicit-function theorem.)
 template <class T>
 __device__ __forceinline__ void qpiece_project(const QPieceT<T> &q, T y0, T h0, T &yo, T &ho)
 {
@@ -176,19 +176,29 @@ __device__ __forceinline__ void qpiece_project(const QPieceT<T> &q, T y0, T h0, 
     }
     if (!q.arc || val(q.m1 - y0 + e1 * q.t1) >= 0.0f) { yo = q.m1; ho = ph1; return; }
     if (val(q.m2 - y0 + e2 * q.t2) <= 0.0f) { yo = q.m2; ho = ph2; return; }
-    // parabola arc
+    // parabola arc: the closed-form root w of the cubic in w
     const T ia = 1.0f / q.a;
     const T p = 2.0f - q.c * q.c - 2.0f * h0 * ia;
     const T qq = -2.0f * (q.c + y0 * ia);
     const float sg = val(qq) <= 0.0f ? 1.0f : -1.0f;
     T w = T(sg * cubic_outer_root(val(p), fabsf(val(qq))));
     w = tmin(tmax(w, q.t1), q.t2);
-    const T F = (w * w + p) * w + qq;
-    const T dF = 3.0f * w * w + p;
-    if (val(dF) > 0.0f) w = tmin(tmax(w - F / dF, q.t1), q.t2);
-    const T y = q.a * (w - q.c);
+    // one Newton step on the offset d = w - c = y/a from the centre, whose
+    // cubic d^3 + 3c d^2 + (2 + 2c^2 - 2 h0/a) d - 2 (c h0 + y0)/a = 0 is the
+    // one above shifted by c; its derivative grows like c^2, so the step is
+    // accurate to the rounding of d itself, and y = a d, rho_i^*(y) =
+    // y (c + d/2) lose nothing to a centre c far from 0 (periodic pieces sit
+    // up to the top of the label range), as w - c and w^2 - c^2 would
+    T d = w - q.c;
+    const T b2 = 3.0f * q.c;
+    const T b1 = 2.0f + 2.0f * q.c * q.c - 2.0f * h0 * ia;
+    const T b0 = -2.0f * (q.c * h0 + y0) * ia;
+    const T F = ((d + b2) * d + b1) * d + b0;
+    const T dF = (3.0f * d + 2.0f * b2) * d + b1;
+    if (val(dF) > 0.0f) d = tmin(tmax(d - F / dF, q.t1 - q.c), q.t2 - q.c);
+    const T y = q.a * d;
     yo = y;
-    ho = 0.5f * q.a * (w * w - q.c * q.c);
+    ho = y * (q.c + 0.5f * d);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,21 +371,13 @@ __device__ __forceinline__ float data_rho(const LiftParams &P, int pix, float t)
         return (1.0f - a) * __ldg(c + j) + a * __ldg(c + j + 1);
     }
     if (P.kind == 3) {
-        // the piece of the interval holding t; within 1e-4 of an interval width of
-        // a label (single-precision rounding of a value on it) the smaller of the two
-        const float x = (t - P.gmin) * P.inv_delta;
-        int i0 = static_cast<int>(floorf(x));
-        i0 = i0 < 0 ? 0 : (i0 > P.k - 1 ? P.k - 1 : i0);
+        // alpha/2 times the squared circular distance to f (period nu): the
+        // nearer of the copies f + nu m, m = floor((t - f)/nu), and the next
         const float f = __ldg(P.f + pix);
-        auto piece = [&](int i) {
-            const float l = P.gmin + P.delta * i;
-            const float d = t - periodic_center(f, P.nu, l, l + P.delta);
-            return 0.5f * P.alpha * d * d;
-        };
-        float best = piece(i0);
-        if (x - i0 < 1e-4f && i0 > 0) best = fminf(best, piece(i0 - 1));
-        if (static_cast<float>(i0 + 1) - x < 1e-4f && i0 + 1 < P.k) best = fminf(best, piece(i0 + 1));
-        return best;
+        const float m = floorf((t - f) / P.nu);
+        const float d1 = t - f - P.nu * m, d2 = d1 - P.nu;
+        const float d = fabsf(d1) < fabsf(d2) ? d1 : d2;
+        return 0.5f * P.alpha * d * d;
     }
     const float d = t - __ldg(P.f + pix);
     if (P.kind == 0) return 0.5f * P.alpha * d * d;

@@ -72,3 +72,14 @@ def oracle_run(c: dict, iters: int):
     X = O.State(P)
     O.pdhg(P, X, iters)
     return P, X
+
+
+def crop_oracle_pixel(job):
+    """Worker for parity at full size: run the oracle on a crop and return
+    the unlifted value and the state rows of one pixel of it.  job = (case,
+    (y0, y1, x0, x1), iters, (py, px)) with (py, px) in image coordinates."""
+    c, (y0, y1, x0, x1), iters, (py_, px_) = job
+    P, X = oracle_run(crop(c, y0, y1, x0, x1), iters)
+    j = (py_ - y0) * (x1 - x0) + (px_ - x0)
+    rows = {name: np.array(getattr(X, name)[j]) for name in ("u", "s", "v", "z", "px", "py")}
+    return float(O.unlift(P, X.u)[j]), rows

@@ -39,3 +39,22 @@ def test_quadratic_piece_conjugate(row):
     val, arg = O.conj(P, 0, int(i), y)
     assert abs(val - c) <= 1e-12, (val, c)
     assert abs(arg - t) <= 1e-12, (arg, t)
+
+
+@pytest.mark.parametrize("row", list(golden("trunc_chain.txt")))
+def test_truncated_chain_closed_form(row):
+    """Truncated-quadratic data (Sec. 5.2) on 1-D chains of two and three
+    pixels: at convergence the unlifted image is the hand-derived optimum and
+    P, D and the nonconvex energy E_nc all meet its energy."""
+    _, L, lam, f1, f2, f3, u1, u2, u3, E = row
+    f = np.array([f1, f2, f3] if f3 >= 0 else [f1, f2])
+    want = np.array([u1, u2, u3] if f3 >= 0 else [u1, u2])
+    P = O.Problem(O.TRUNC, 1, len(f), int(L), 0.0, 1.0, lam=lam, alpha=25.0, nu=0.1, f=f)
+    X = O.State(P)
+    O.pdhg(P, X, 60000)
+    ut = O.unlift(P, X.u)
+    assert np.abs(ut - want).max() <= 1e-7, ut
+    Ph, D, Enc = O.energy(P, X)
+    assert D <= E + 1e-9 and Ph >= E - 1e-9
+    for v in (Ph, D, Enc):
+        assert abs(v - E) <= 1e-7, (v, E)

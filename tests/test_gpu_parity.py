@@ -4,6 +4,8 @@ Tolerances: the unlifted image within 1e-4 max-abs after normalising by the
 label range, energies within 1e-5 relative, after a fixed iteration count;
 single projections and envelopes within a few FP32 ulps of the point's scale.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -213,42 +215,70 @@ def test_lambda_zero_and_zero_iterations():
 # (clipped at the true image border) reproduces it exactly.
 # ---------------------------------------------------------------------------
 def _sampled_parity(c, iters, samples, seed):
-    H, W = c["H"], c["W"]
-    with gpu_solver(c) as s:
+    """The full-size problem on the GPU, as the bench runs it (the iteration
+    graph, banded where the size asks for it), against the oracle on crops
+    around sampled pixels: the three corners, `samples` random pixels, the
+    first and last pixel of every band of the graph, and pixels on both sides
+    of a dual-step strip boundary.  One iteration spreads a pixel's influence
+    one pixel along each axis (the dual step reads x+1, y+1, the primal step
+    x-1, y-1), so a crop margin of 2 iters + 2 pixels leaves the sampled
+    pixel's iterate exactly that of the full image.  The crops run in
+    parallel processes (started with spawn)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    from _cases import crop_oracle_pixel
+    from paper_1512_01383_gb300 import lift as G
+    H, W, L = c["H"], c["W"], c["L"]
+    k = L - 1
+    with gpu_solver(c, check_every=iters // 2) as s:
+        bands = G.lift_set_bands(s.h, 0)
         s.iterate(iters)
         ut = s.unlift()
         st = s.state()
-    m = 2 * iters + 2
+    # band boundaries of the graph (tiles of 256 // k pixels, cut at even tiles)
+    ppb = 256 // k
+    T = (H * W + ppb - 1) // ppb
+    cuts = [(T * j // bands) // 2 * 2 * ppb for j in range(1, bands)]
     rng = np.random.default_rng(seed)
-    pts = [(0, 0), (H - 1, W - 1), (0, W - 1)] + [
-        (int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(samples)]
+    flat = [0, H * W - 1, W - 1, 64 * 37 - 1, 64 * 37]
+    for b in cuts:
+        flat += [b - 1, b]
+    flat += [int(v) for v in rng.integers(0, H * W, samples)]
+    pts = sorted({(p // W, p % W) for p in flat})
+    m = 2 * iters + 2
+    jobs = []
     for (py_, px_) in pts:
-        y0, y1 = max(0, py_ - m), min(H, py_ + m + 1)
-        x0, x1 = max(0, px_ - m), min(W, px_ + m + 1)
-        cc = crop(c, y0, y1, x0, x1)
-        P, X = oracle_run(cc, iters)
-        j = (py_ - y0) * (x1 - x0) + (px_ - x0)
-        ur = O.unlift(P, X.u)[j]
-        rngl = c["gamma_max"] - c["gamma_min"]
+        box = (max(0, py_ - m), min(H, py_ + m + 1), max(0, px_ - m), min(W, px_ + m + 1))
+        jobs.append((c, box, iters, (py_, px_)))
+    with ProcessPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        results = list(ex.map(crop_oracle_pixel, jobs))
+    rngl = c["gamma_max"] - c["gamma_min"]
+    for (py_, px_), (ur, rows) in zip(pts, results):
         assert abs(ut[py_, px_] - ur) / rngl <= U_TOL, (py_, px_, ut[py_, px_], ur)
         g = py_ * W + px_
-        for name in ("u", "s", "v", "z", "px", "py"):
-            a, b = st[name][g], getattr(X, name)[j]
+        for name, b in rows.items():
+            a = st[name][g]
             assert np.abs(a - b).max() <= 2e-3 * (1 + np.abs(b).max()), (name, a, b)
+    return len(pts)
 
 
 @pytest.mark.parametrize("L", [5, 10, 20])
 def test_full_size_truncated_512(L):
+    """512 x 512 truncated quadratic (the bench's workload at L = 20), 50
+    iterations, in the banded graph."""
     _require_gpu()
     c = case(1, 512, 512, L, 1512013832)
-    _sampled_parity(c, 3, 5, L)
+    assert _sampled_parity(c, 50, 8, L) >= 14
 
 
 @pytest.mark.parametrize("L", [8, 32])
 def test_full_size_stereo_640x480(L):
+    """640 x 480 stereo costs (PL pieces), 50 iterations."""
     _require_gpu()
     c = case(2, 480, 640, L, 1512013834, ndisp=65)
-    _sampled_parity(c, 2, 3, L)
+    assert _sampled_parity(c, 50, 8, L) >= 11
 
 
 # ---------------------------------------------------------------------------
@@ -380,11 +410,8 @@ def test_phase_unwrapping_matches_oracle(H, W, L, iters):
     assert np.abs(ut.reshape(-1) - O.unlift(P, X.u)).max() / rng <= U_TOL
     _compare_state(st, X, P, 2e-3)
     Po, Do, Eo = O.energy(P, X)
-    # labels on [0, 4 pi] carry larger dual values, so the FP32 and FP64
-    # trajectories part a little more than on [0, 1]; the energy kernel
-    # itself stays at 1e-5 on a shared state (test_energy_kernel_on_oracle_state)
     for g, o in ((Pg, Po), (Dg, Do), (Eg, Eo)):
-        assert abs(g - o) <= 5 * E_TOL * max(abs(o), 1.0), (g, o)
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
 
 
 @pytest.mark.parametrize("L,iters", [(5, 200), (12, 150)])
@@ -428,5 +455,27 @@ def test_two_pixel_rof_golden(resident):
             ut = s.unlift().reshape(-1)
             Pg, Dg, Eg = s.energy()
         assert np.abs(ut - [u1, u2]).max() <= 2e-6, (ut, u1, u2)
+        for v in (Pg, Dg, Eg):
+            assert abs(v - E) <= 1e-6, (v, E)
+
+
+@pytest.mark.parametrize("resident", [True, False])
+def test_truncated_chain_golden(resident):
+    """The hand-derived truncated-quadratic chains of tests/golden/trunc_chain.txt
+    (Sec. 5.2) on the GPU: after 60 000 iterations the unlifted image and the
+    energies meet them within FP32 rounding."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    from test_golden import golden
+    for _, L, lam, f1, f2, f3, u1, u2, u3, E in golden("trunc_chain.txt"):
+        fv = [f1, f2, f3] if f3 >= 0 else [f1, f2]
+        want = [u1, u2, u3] if f3 >= 0 else [u1, u2]
+        f = torch.tensor([fv], dtype=torch.float32, device="cuda")
+        with G.Solver(G.LIFT_TRUNC_QUAD, 1, len(fv), int(L), 0.0, 1.0, lam, 25.0, 0.1, f=f,
+                      resident=resident) as s:
+            s.iterate(60000)
+            ut = s.unlift().reshape(-1)
+            Pg, Dg, Eg = s.energy()
+        assert np.abs(ut - want).max() <= 2e-6, (ut, want)
         for v in (Pg, Dg, Eg):
             assert abs(v - E) <= 1e-6, (v, E)

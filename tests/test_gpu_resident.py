@@ -76,10 +76,9 @@ def test_resident_matches_oracle_and_per_step_kernels(kind, H, W, L, iters, extr
     assert np.abs(ua.reshape(-1) - O.unlift(P, X.u)).max() / rng <= U_TOL
     assert np.abs(ua - ub).max() / rng <= U_TOL
     _compare_state(sa, X, P, 2e-3)
-    etol = 5 * E_TOL if kind == 3 else E_TOL
     for g, h, o in zip(ea, eb, O.energy(P, X)):
-        assert abs(g - o) <= etol * max(abs(o), 1.0), (g, o)
-        assert abs(g - h) <= etol * max(abs(h), 1.0), (g, h)
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (g, o)
+        assert abs(g - h) <= E_TOL * max(abs(h), 1.0), (g, h)
 
 
 def test_resident_calls_compose():

@@ -98,7 +98,7 @@ def _check(c, iters, etol=E_TOL):
 def test_volume_iterations_match_oracle(kind, D, H, W, L, iters, aniso):
     _require_gpu()
     c = vcase(kind, D, H, W, L, 2000 + 7 * D + L, aniso=aniso)
-    _check(c, iters, 5 * E_TOL if kind == 3 else E_TOL)
+    _check(c, iters, E_TOL)
 
 
 @pytest.mark.parametrize("D,H,W,L", [(2, 1, 37, 5), (9, 1, 1, 4), (3, 5, 1, 6), (7, 2, 3, 3)])

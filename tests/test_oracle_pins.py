@@ -611,6 +611,29 @@ def test_periodic_pieces_conjugate_and_envelope():
     assert O.rho(P, 0, t) == pytest.approx(0.5 * d * d)
 
 
+def test_periodic_rho_is_the_squared_circular_distance():
+    """rho of the phase-unwrapping term (Sec. 5.5) is alpha/2 times the
+    squared circular distance to f: against the minimum over 21 copies
+    f + 2 pi m, at random points, exactly at the labels, one rounding step
+    to either side of them, and half a period from f (the two nearest copies
+    tie there)."""
+    per, alpha = 2 * np.pi, 1.7
+    w, _ = synth.wrapped_phase(3, 4, 159)
+    L = 8
+    P = O.Problem(O.PERIODIC, 3, 4, L, 0.0, 4 * np.pi, lam=0.1, alpha=alpha, nu=per, f=w)
+    lab = O.labels(L, 0.0, 4 * np.pi)
+    r = synth.Rng(160)
+    ms = np.arange(-10, 11)
+    for pix in range(P.N):
+        f = P.f[pix]
+        pts = list(r.uniform(40, -1.0, 4 * np.pi + 1.0)) + list(lab)
+        pts += [np.nextafter(x, -np.inf) for x in lab] + [np.nextafter(x, np.inf) for x in lab]
+        pts += [f + 0.5 * per, f + 1.5 * per, f - 0.5 * per]
+        for t in pts:
+            want = 0.5 * alpha * np.min((t - f - per * ms) ** 2)
+            assert abs(O.rho(P, pix, t) - want) <= 1e-12 * (1.0 + want), (pix, t)
+
+
 def test_phase_unwrapping_recovers_the_ramp():
     """A wrapped 1-D phase ramp from 1 to 11 rad (wraps twice) is unwrapped by
     the relaxation with 8 labels on [0, 4 pi]: errors far below pi."""
@@ -650,3 +673,6 @@ def test_periodic_lambda0_circular_distance():
         errs.append(np.abs(O.unlift(P, X.u) - tc).max())
     assert gaps[-1] < 0.1 * gaps[0] and gaps[-1] < 2e-3 * max(opt, 1.0)
     assert errs[-1] < 1e-2, errs
+    # the nonconvex energy of the unlifted image (rho itself, the squared
+    # circular distance; no TV at lambda = 0) reaches the same optimum
+    assert abs(E - opt) <= 2e-3 * max(opt, 1.0), (E, opt)
