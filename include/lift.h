@@ -279,9 +279,18 @@ int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every);
  * be NULL) and {dL/dlambda, dL/dalpha, dL/dnu} to grad_scalars (host, 3
  * doubles; may be NULL).  Each segment between checkpoints is recomputed
  * forward into a buffer of checkpoint_every + 1 states, then pulled back.
- * Synchronises when grad_scalars is requested. */
+ * Synchronises when grad_scalars is requested.  LIFT_ERR_ARG if no forward
+ * pass is stored, or if lift_set_params, lift_set_data or lift_reset has run
+ * since the last one (the stored pass would no longer be this problem's). */
 int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f,
                            double *grad_scalars);
+
+/* lift_unrolled_generation: a counter that changes with every
+ * lift_unrolled_forward, lift_set_params, lift_set_data and lift_reset of
+ * the handle.  A caller that keeps the value of a forward pass (as the
+ * autograd wrapper does) can tell, before its reverse pass, whether the
+ * handle still holds that forward pass. */
+int lift_unrolled_generation(lift_handle h, unsigned long long *generation);
 
 /* --------------------------------------------------------------- batches */
 /* A batch solves many independent problems (each its own size, label count
@@ -370,7 +379,8 @@ int lift_batch_schedule(lift_batch b, int *threads, int *big_tiles, int *n_big);
  *        in the layout of lift_get_state (only the primal and dual parts are
  *        read).
  * out    device pointer to 3 doubles: {primal_relaxed, dual, e_nonconvex}.
- * stream cudaStream_t for the two kernels; the call is asynchronous and
+ * stream cudaStream_t of the current device for the two kernels (a stream
+ *        of another device gives LIFT_ERR_ARG); the call is asynchronous and
  *        does not synchronise.
  *
  * The per-block partial sums go to one fixed array in the library's device

@@ -39,6 +39,9 @@ struct lift_ctx {
     char *ckpt = nullptr;      // checkpoints: states at iterations 0, C, 2C, ...
     char *seg = nullptr;       // one segment's states, recomputed in the backward pass
     int unrolled_iters = 0, ckpt_every = 0, ckpt_count = 0, seg_cap = 0;
+    // bumped by every call that changes what a reverse pass would
+    // differentiate (forward, parameters, data, reset)
+    unsigned long long generation = 0;
     lift::AdjState adj{};
     void *adj_arena = nullptr;
     // graph replay of whole check intervals (lift_iterate)
@@ -433,15 +436,24 @@ void lift_destroy(lift_handle h)
     free_ctx(h);
 }
 
+// The stored forward no longer matches the handle: a reverse pass now fails.
+static void invalidate_unrolled(lift_handle h)
+{
+    h->unrolled_iters = 0;
+    ++h->generation;
+}
+
 int lift_set_data(lift_handle h, const float *data, int on_host)
 {
     if (!h || !data) return LIFT_ERR_ARG;
+    invalidate_unrolled(h);
     return upload_data(h, data, on_host);
 }
 
 int lift_reset(lift_handle h)
 {
     if (!h) return LIFT_ERR_ARG;
+    invalidate_unrolled(h);
     const size_t Nk = static_cast<size_t>(h->N) * h->k;
     LIFT_CK(cudaMemsetAsync(h->S.x, 0, Nk * sizeof(float2), h->stream));
     LIFT_CK(cudaMemsetAsync(h->S.xbar, 0, Nk * sizeof(float2), h->stream));
@@ -1339,6 +1351,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
         if (!is_finite(alpha) || !(alpha > 0.0)) return LIFT_ERR_SPEC;
         if (h->kind != LIFT_QUAD && (!is_finite(nu) || !(nu > 0.0))) return LIFT_ERR_SPEC;
     }
+    invalidate_unrolled(h);
     std::vector<float4> ic(h->k);
     LIFT_CK(cudaMemcpyAsync(ic.data(), h->icst, h->k * sizeof(float4), cudaMemcpyDeviceToHost, h->stream));
     LIFT_CK(cudaStreamSynchronize(h->stream));
@@ -1381,6 +1394,14 @@ int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every)
     }
     h->unrolled_iters = iters;
     h->ckpt_every = checkpoint_every;
+    ++h->generation;
+    return LIFT_OK;
+}
+
+int lift_unrolled_generation(lift_handle h, unsigned long long *generation)
+{
+    if (!h || !generation) return LIFT_ERR_ARG;
+    *generation = h->generation;
     return LIFT_OK;
 }
 

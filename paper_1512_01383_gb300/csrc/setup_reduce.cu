@@ -437,6 +437,14 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LIFT_ERR_CUDA;
     if (dev < 0 || dev >= kNoAllocDevices) return LIFT_ERR_ARG;
+    // the array's address is the current device's: a stream of another
+    // device would run the kernels against the wrong memory
+    if (stream) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev) != cudaSuccess)
+            return LIFT_ERR_CUDA;
+        if (sdev != dev) return LIFT_ERR_ARG;
+    }
     double *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);

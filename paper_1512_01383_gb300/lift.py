@@ -31,7 +31,7 @@ EXPORTED = (
     "lift_batch_get_state", "lift_batch_autotune", "lift_batch_schedule",
     "lift_batch_set_schedule",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
-    "lift_get_balance", "lift_set_resident", "lift_set_bands",
+    "lift_get_balance", "lift_set_resident", "lift_set_bands", "lift_unrolled_generation",
 )
 
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "lift_get_balance": (C.c_int, [vp, dp]),
         "lift_set_resident": (C.c_int, [vp, C.c_int, ip]),
         "lift_set_bands": (C.c_int, [vp, C.c_int, ip]),
+        "lift_unrolled_generation": (C.c_int, [vp, C.POINTER(C.c_ulonglong)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -256,7 +257,21 @@ def lift_envelope(h: int, pix, interval, t, out) -> None:
 
 def lift_energy_noalloc(spec: lift_spec, state, out, stream: int | None = None) -> None:
     """Energies of a caller-held device state into out[3] (device), with no
-    allocation (see include/lift.h)."""
+    allocation (see include/lift.h).  The C entry point cannot see buffer
+    sizes, so they are checked here: out must be a CUDA float64 tensor of at
+    least 3 elements, state a CUDA tensor holding at least the primal and dual
+    records of the problem (H*W*(L-1) * 32 bytes, the x, xbar and y parts of
+    the lift_get_state layout)."""
+    import torch
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+            and out.numel() >= 3 and out.is_contiguous()):
+        raise LiftError(LIFT_ERR_ARG, "lift_energy_noalloc: out must be a contiguous CUDA "
+                                      "float64 tensor of at least 3 elements")
+    need = spec.H * spec.W * (spec.L - 1) * 32
+    if not (isinstance(state, torch.Tensor) and state.is_cuda and state.is_contiguous()
+            and state.numel() * state.element_size() >= need):
+        raise LiftError(LIFT_ERR_ARG, f"lift_energy_noalloc: state must be a contiguous CUDA "
+                                      f"tensor of at least {need} bytes")
     s = current_stream() if stream is None else stream
     _check(load().lift_energy_noalloc(C.byref(spec), C.c_void_p(state.data_ptr()),
                                       C.c_void_p(out.data_ptr()), C.c_void_p(s)),
@@ -471,6 +486,14 @@ def lift_set_params(h: int, lam: float, alpha: float, nu: float) -> None:
 def lift_unrolled_forward(h: int, iters: int, checkpoint_every: int) -> None:
     _check(load().lift_unrolled_forward(C.c_void_p(h), iters, checkpoint_every),
            "lift_unrolled_forward")
+
+
+def lift_unrolled_generation(h: int) -> int:
+    """The handle's forward-pass generation (changes with every unrolled
+    forward, parameter, data or reset call)."""
+    g = C.c_ulonglong(0)
+    _check(load().lift_unrolled_generation(C.c_void_p(h), C.byref(g)), "lift_unrolled_generation")
+    return int(g.value)
 
 
 def lift_unrolled_backward(h: int, grad_u, grad_f=None) -> tuple[float, float, float]:

@@ -102,6 +102,67 @@ def test_autograd_function():
     np.testing.assert_allclose([lam.grad.item(), al.grad.item(), nu.grad.item()], gs2)
 
 
+def test_mid_size_many_segments_match_oracle_reverse_pass():
+    """32 x 32, L = 16, 200 iterations with checkpoints every 50: the
+    reverse pass recomputes four segments, the regime of the 256 x 256
+    configuration, against the oracle's FP64 reverse pass (the observed
+    errors are printed next to the tolerances)."""
+    _require_gpu()
+    H, W, L, iters = 32, 32, 16, 200
+    noisy, clean = synth.voronoi_ramps(H, W, 97)
+    f = synth.as_f32(noisy)
+    with _solver(1, f, L, 0.25, 25.0, 0.1) as s:
+        u, gf, gs = _gpu_grads(s, iters, 50, clean)
+    P = O.Problem(O.TRUNC, H, W, L, 0.0, 1.0, lam=0.25, alpha=25.0, nu=0.1, f=f.astype(np.float64))
+    X = O.State(P)
+    O.pdhg(P, X, iters)
+    uo = O.unlift(P, X.u)
+    assert np.abs(u.reshape(-1) - uo).max() <= 1e-4
+    gfo, gso = O.unrolled_grad(P, iters, 2.0 * (uo - clean.reshape(-1)))
+    scale = np.abs(gfo).max()
+    ef = np.abs(gf.reshape(-1) - gfo).max() / scale
+    es = [abs(g - o) / max(abs(o), 1e-2) for g, o in zip(gs, gso)]
+    print(f"mid-size adjoint: max|dL/df - oracle| / max = {ef:.2e}; "
+          f"scalar relative errors {es[0]:.2e} {es[1]:.2e} {es[2]:.2e}")
+    # observed on a GB300: 1.4e-3 and 1e-5..3e-5 (the scalar sums over many
+    # records average out the branch differences that dominate tiny images)
+    assert ef <= 2e-3
+    for e in es:
+        assert e <= 1e-3, (gs, gso)
+
+
+def test_backward_refuses_a_replaced_forward_pass():
+    """The handle keeps one forward pass: a second unrolled_solve on the
+    same solver, or new parameters, data or a reset, make the reverse pass of
+    the first one fail loudly (the autograd wrapper and the C entry point)."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    from paper_1512_01383_gb300.autograd import unrolled_solve
+    H, W, L, iters = 12, 10, 5, 20
+    noisy, clean = synth.voronoi_ramps(H, W, 96)
+    f = torch.from_numpy(synth.as_f32(noisy)).cuda().requires_grad_(True)
+    cl = torch.from_numpy(clean.astype(np.float32)).cuda()
+    with _solver(1, synth.as_f32(noisy), L, 0.25, 25.0, 0.1) as s:
+        u1 = unrolled_solve(f, 0.25, 25.0, 0.1, s, iters, 5)
+        u2 = unrolled_solve(f, 0.3, 25.0, 0.1, s, iters, 5)
+        with pytest.raises(G.LiftError):
+            ((u1 - cl) ** 2).sum().backward()
+        ((u2 - cl) ** 2).sum().backward()          # the stored pass is u2's
+        assert f.grad is not None and torch.isfinite(f.grad).all()
+        gu = torch.zeros((H, W), device="cuda")
+        for change in (lambda: G.lift_set_params(s.h, 0.2, 25.0, 0.1),
+                       lambda: G.lift_set_data(s.h, torch.from_numpy(synth.as_f32(noisy)).cuda()),
+                       lambda: G.lift_reset(s.h)):
+            G.lift_unrolled_forward(s.h, iters, 5)
+            g0 = G.lift_unrolled_generation(s.h)
+            G.lift_unrolled_backward(s.h, gu)
+            change()
+            assert G.lift_unrolled_generation(s.h) != g0
+            with pytest.raises(G.LiftError) as e:
+                G.lift_unrolled_backward(s.h, gu)
+            assert e.value.code == G.LIFT_ERR_ARG
+
+
 def test_full_size_taylor_check():
     """256x256, L=16, 500 unrolled iterations, checkpoints every 50: the
     gradient is finite, equals that of a single-segment reverse pass, and

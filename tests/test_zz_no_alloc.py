@@ -61,3 +61,16 @@ def test_noalloc_rejects_oversized_and_host_inputs():
     with pytest.raises(G.LiftError) as e:
         G.lift_energy_noalloc(host, state, out)
     assert e.value.code == G.LIFT_ERR_ARG
+    # buffers the wrapper checks before the C call (which cannot see sizes)
+    ok = G.make_spec(G.LIFT_TRUNC_QUAD, 2, 2, 5, 0.0, 1.0, 0.25, 25.0, 0.1, f=f_dev)
+    bad_outs = [torch.zeros(3, dtype=torch.float32, device="cuda"),    # not float64
+                torch.zeros(2, dtype=torch.float64, device="cuda"),    # too short
+                torch.zeros(3, dtype=torch.float64)]                   # on the host
+    for bad in bad_outs:
+        with pytest.raises(G.LiftError) as e:
+            G.lift_energy_noalloc(ok, state, bad)
+        assert e.value.code == G.LIFT_ERR_ARG
+    small = torch.zeros(2 * 2 * 4 * 32 - 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(G.LiftError) as e:
+        G.lift_energy_noalloc(ok, small, out)
+    assert e.value.code == G.LIFT_ERR_ARG
