@@ -513,6 +513,65 @@ def run_reference(args):
     return 0
 
 
+def run_bands(args, G, torch, dist, rank, world, dev, barrier):
+    """One (512 world) x 512 image split into bands of 512 rows, one per rank
+    (the spatial decomposition of the grid of Sec. 4): per iteration the
+    first own row's primal records go to the rank above and the last own
+    row's dual records to the rank below (NCCL point to point), and at each
+    check the three FP64 energy sums are all-reduced.  Weak scaling: the
+    pixels per rank stay 512 x 512."""
+    from paper_1512_01383_gb300.bands import DistributedBand, HandleBand
+    Hg = H * world
+    # the whole image's data: rank r's band is the replica input of rank r
+    fg = np.concatenate([make_input(r) for r in range(world)], axis=0)
+    fd = torch.from_numpy(fg).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    spec = G.make_spec(G.LIFT_TRUNC_QUAD, Hg, W, L, 0.0, 1.0, LAM, ALPHA, NU, f=fd,
+                       check_every=ITERS_PER_STEP, step_balance=THETA)
+    band = HandleBand(spec, rank * H, (rank + 1) * H, stream.cuda_stream)
+    sched = DistributedBand(band, rank, world,
+                            lambda n: torch.empty(n, dtype=torch.uint8, device=dev))
+    uout = torch.empty((H, W), device=dev)
+    energy_buf = []
+
+    def step():
+        sched.iterate(ITERS_PER_STEP)
+        energy_buf.append(sched.energy(dev))      # FP64 all_reduce of the three sums
+        band.unlift(uout)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    units = H * W * K_INT * ITERS_PER_STEP * args.steps * world
+    value = units / (ms * 1e-3) / 1e9
+    if rank == 0:
+        P, Dl, E = energy_buf[-1]
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f"; one {Hg}x{W} image in {world} bands of {H} rows",
+                       "H": Hg, "W": W, "L": L, "k": K_INT, "iters_per_step": ITERS_PER_STEP,
+                       "parallelism": f"bands{world}",
+                       "l2": "inputs larger than L2 (160 MB state per rank)"},
+            "gpu_launches": args.steps * (2 * ITERS_PER_STEP + 3),
+            "clocks": clk.summary(),
+            "final_energy": {"primal": P, "dual": Dl, "nonconvex": E},
+        }))
+    band.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +581,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true", help="skip the time-to-gap runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve section")
+    ap.add_argument("--parallelism", choices=["replicas", "bands"], default="replicas",
+                    help="replicas: every rank solves its own 512x512 problem; bands: the ranks "
+                         "share one (512 N) x 512 image, a band of 512 rows each, halo rows "
+                         "exchanged between neighbours before each half-step")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ROF, stereo, differentiable, phase, baseline-lifting and volume "
                          "sections")
@@ -549,6 +612,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    if args.parallelism == "bands":
+        return run_bands(args, G, torch, dist, rank, world, dev, barrier)
     f = make_input(rank)
     fd = torch.from_numpy(f).to(dev)
     stream = torch.cuda.current_stream(dev)

@@ -292,6 +292,53 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f,
  * handle still holds that forward pass. */
 int lift_unrolled_generation(lift_handle h, unsigned long long *generation);
 
+/* ------------------------------------------------------ bands of an image */
+/* Spatial decomposition of one image problem over several handles (one per
+ * GPU, or several on one GPU): each handle owns a band of consecutive rows.
+ * The operator of Sec. 4 couples a pixel only to its forward-difference
+ * neighbours (x+1, y+1 in grad, x-1, y-1 in div), so a band needs one row of
+ * its neighbours per half-step and exchanges nothing else: per iteration
+ *   1. every band but the first exports LIFT_HALO_PRIMAL (its first own
+ *      row's x and xbar records); the band above imports it;
+ *   2. every band runs lift_dual_step (its own rows only);
+ *   3. every band but the last exports LIFT_HALO_DUAL (its last own row's y
+ *      records); the band below imports it;
+ *   4. every band runs lift_primal_step (its own rows only).
+ * The own rows then evolve exactly as in one handle over the whole image
+ * (the same arithmetic per record, in the same order).  lift_energy of a
+ * band returns the sums over its own pixels; the three sums of the whole
+ * image are the sums over the bands (an FP64 allreduce across ranks).  The
+ * energies read the row below through the halo, so call it after step 1.
+ * lift_unlift writes the band's own rows.  lift_iterate, lift_solve,
+ * lift_gap and the unrolled solve return LIFT_ERR_ARG on a band (they would
+ * skip the exchanges); the caller runs the loop above. */
+#define LIFT_HALO_PRIMAL 0   /* x then xbar records of one row: 2 W k float2 */
+#define LIFT_HALO_DUAL   1   /* y records of one row: W k float4             */
+
+/* lift_create_band: a handle for the rows [row0, row1) of the image that
+ * *spec describes (its H, W, data pointer and parameters are those of the
+ * whole image; the band reads the data rows it needs, its own and the halo
+ * rows, at create).  Images only.  Errors as lift_create; LIFT_ERR_ARG for
+ * an empty or out-of-range row interval. */
+int lift_create_band(const lift_spec *spec, int row0, int row1, void *stream, lift_handle *out);
+
+/* lift_band_halo_bytes: the size of a halo of kind `which` (a row of W
+ * pixels).  LIFT_ERR_ARG for a handle that is not a band. */
+int lift_band_halo_bytes(lift_handle h, int which, size_t *bytes);
+
+/* lift_band_export: copy the band's halo of kind `which` into dst (device
+ * or host per on_host, lift_band_halo_bytes bytes), in stream order on the
+ * handle's stream (synchronised when on_host).  LIFT_ERR_ARG when no band
+ * receives it (LIFT_HALO_PRIMAL of the first band, LIFT_HALO_DUAL of the
+ * last). */
+int lift_band_export(lift_handle h, int which, void *dst, int on_host);
+
+/* lift_band_import: copy a neighbour's exported halo from src into this
+ * band's halo row (LIFT_HALO_PRIMAL: the row below its own rows;
+ * LIFT_HALO_DUAL: the row above), in stream order on the handle's stream.
+ * LIFT_ERR_ARG when the band has no such neighbour. */
+int lift_band_import(lift_handle h, int which, const void *src, int on_host);
+
 /* --------------------------------------------------------------- batches */
 /* A batch solves many independent problems (each its own size, label count
  * and data; one quadratic data-term kind: LIFT_QUAD, LIFT_TRUNC_QUAD or

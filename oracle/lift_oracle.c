@@ -456,10 +456,79 @@ void orc_steps_get(const orc_problem *P, double *tau_u, double *sigma_q,
 /* of rho_i^* (eq. equality_constr_data), then primal descent on (u, s)     */
 /* with u kept in [0,1]^k, then extrapolation with theta = 1.               */
 /* ------------------------------------------------------------------------ */
-int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
+/* The dual half-step: TV dual ascent and projection onto K, data-dual ascent
+   and projection onto the scaled epigraphs, q ascent.  gx, gy, gz: Nk work. */
+static void dual_half(const orc_problem *P, orc_state *X, const orc_steps *S, double *gx,
+                      double *gy, double *gz)
 {
     int H = P->H, W = P->W, k = P->L - 1, Dz = depth(P);
-    size_t N = npix(P), Nk = N * k;
+    size_t N = npix(P);
+    orc_grad3(Dz, H, W, k, X->ubar, gx, gy, gz);
+    for (size_t pix = 0; pix < N; ++pix) {
+        double *v = X->v + pix * k, *z = X->z + pix * k;
+        double *px = X->px + pix * k, *py = X->py + pix * k;
+        const double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
+        /* TV dual: ascent, then projection onto |p_i| <= lambda Delta_i */
+        for (int i = 0; i < k; ++i) {
+            double d = gam(P, i + 1) - gam(P, i);
+            double ax = px[i] + S->sigma_p * gx[pix * k + i];
+            double ay = py[i] + S->sigma_p * gy[pix * k + i];
+            double az = Dz > 1 ? X->pz[pix * k + i] + S->sigma_p * gz[pix * k + i] : 0.0;
+            tv_project(P->aniso, P->lam * d, &ax, &ay, &az);
+            px[i] = ax;
+            py[i] = ay;
+            if (Dz > 1) X->pz[pix * k + i] = az;
+        }
+        /* data duals: ascent on v, z, q */
+        double tot = 0.0;
+        for (int i = 0; i < k; ++i) tot += (gam(P, i + 1) - gam(P, i)) * sb[i];
+        for (int l = 0; l < k; ++l) {
+            double tail = 0.0;
+            for (int j = l + 1; j < k; ++j) tail += (gam(P, j + 1) - gam(P, j)) * sb[j];
+            v[l] += S->sigma_vz[l] * (ub[l] + tail - gam(P, l) * sb[l]);
+            z[l] += S->sigma_vz[l] * sb[l];
+        }
+        X->q[pix] -= S->sigma_q * (1.0 + tot);
+        /* projection of (v_i, z_i) onto Delta_i * epi(rho_i^*) */
+        for (int i = 0; i < k; ++i) {
+            double d = gam(P, i + 1) - gam(P, i);
+            double yo, ho;
+            orc_proj_epi(P, (int)pix, i, v[i] / d, z[i] / d, &yo, &ho);
+            v[i] = d * yo;
+            z[i] = d * ho;
+        }
+    }
+}
+
+/* The primal half-step: descent on (u, s), u clamped to [0,1]^k, then the
+   extrapolation (theta = 1).  dv: Nk work. */
+static void primal_half(const orc_problem *P, orc_state *X, const orc_steps *S, double *dv)
+{
+    int H = P->H, W = P->W, k = P->L - 1, Dz = depth(P);
+    size_t N = npix(P);
+    orc_div3(Dz, H, W, k, X->px, X->py, Dz > 1 ? X->pz : NULL, dv);
+    for (size_t pix = 0; pix < N; ++pix) {
+        const double *v = X->v + pix * k, *z = X->z + pix * k;
+        double *u = X->u + pix * k, *s = X->s + pix * k;
+        double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
+        double q = X->q[pix], prefix = 0.0;
+        for (int i = 0; i < k; ++i) {
+            double d = gam(P, i + 1) - gam(P, i);
+            double un = clampd(u[i] - S->tau_u * (v[i] - dv[pix * k + i]), 0.0, 1.0);
+            double sn = s[i] - S->tau_s[i] * (z[i] - d * q + d * prefix - gam(P, i) * v[i]);
+            prefix += v[i];
+            ub[i] = 2.0 * un - u[i];
+            sb[i] = 2.0 * sn - s[i];
+            u[i] = un;
+            s[i] = sn;
+        }
+    }
+}
+
+int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
+{
+    int k = P->L - 1, Dz = depth(P);
+    size_t Nk = npix(P) * k;
     if (Dz > 1 && !X->pz) return -2;
     orc_steps S;
     make_steps(P, &S);
@@ -470,64 +539,33 @@ int orc_pdhg(const orc_problem *P, orc_state *X, int iters)
     if (!gx || !gy || !gz || !dv) {
         free(gx); free(gy); free(gz); free(dv); free_steps(&S); return -1;
     }
-
     for (int n = 0; n < iters; ++n) {
-        /* ---- dual step ---- */
-        orc_grad3(Dz, H, W, k, X->ubar, gx, gy, gz);
-        for (size_t pix = 0; pix < N; ++pix) {
-            double *v = X->v + pix * k, *z = X->z + pix * k;
-            double *px = X->px + pix * k, *py = X->py + pix * k;
-            const double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
-            /* TV dual: ascent, then projection onto |p_i| <= lambda Delta_i */
-            for (int i = 0; i < k; ++i) {
-                double d = gam(P, i + 1) - gam(P, i);
-                double ax = px[i] + S.sigma_p * gx[pix * k + i];
-                double ay = py[i] + S.sigma_p * gy[pix * k + i];
-                double az = Dz > 1 ? X->pz[pix * k + i] + S.sigma_p * gz[pix * k + i] : 0.0;
-                tv_project(P->aniso, P->lam * d, &ax, &ay, &az);
-                px[i] = ax;
-                py[i] = ay;
-                if (Dz > 1) X->pz[pix * k + i] = az;
-            }
-            /* data duals: ascent on v, z, q */
-            double tot = 0.0;
-            for (int i = 0; i < k; ++i) tot += (gam(P, i + 1) - gam(P, i)) * sb[i];
-            for (int l = 0; l < k; ++l) {
-                double tail = 0.0;
-                for (int j = l + 1; j < k; ++j) tail += (gam(P, j + 1) - gam(P, j)) * sb[j];
-                v[l] += S.sigma_vz[l] * (ub[l] + tail - gam(P, l) * sb[l]);
-                z[l] += S.sigma_vz[l] * sb[l];
-            }
-            X->q[pix] -= S.sigma_q * (1.0 + tot);
-            /* projection of (v_i, z_i) onto Delta_i * epi(rho_i^*) */
-            for (int i = 0; i < k; ++i) {
-                double d = gam(P, i + 1) - gam(P, i);
-                double yo, ho;
-                orc_proj_epi(P, (int)pix, i, v[i] / d, z[i] / d, &yo, &ho);
-                v[i] = d * yo;
-                z[i] = d * ho;
-            }
-        }
-        /* ---- primal step ---- */
-        orc_div3(Dz, H, W, k, X->px, X->py, Dz > 1 ? X->pz : NULL, dv);
-        for (size_t pix = 0; pix < N; ++pix) {
-            const double *v = X->v + pix * k, *z = X->z + pix * k;
-            double *u = X->u + pix * k, *s = X->s + pix * k;
-            double *ub = X->ubar + pix * k, *sb = X->sbar + pix * k;
-            double q = X->q[pix], prefix = 0.0;
-            for (int i = 0; i < k; ++i) {
-                double d = gam(P, i + 1) - gam(P, i);
-                double un = clampd(u[i] - S.tau_u * (v[i] - dv[pix * k + i]), 0.0, 1.0);
-                double sn = s[i] - S.tau_s[i] * (z[i] - d * q + d * prefix - gam(P, i) * v[i]);
-                prefix += v[i];
-                ub[i] = 2.0 * un - u[i];
-                sb[i] = 2.0 * sn - s[i];
-                u[i] = un;
-                s[i] = sn;
-            }
-        }
+        dual_half(P, X, &S, gx, gy, gz);
+        primal_half(P, X, &S, dv);
     }
     free(gx); free(gy); free(gz); free(dv);
+    free_steps(&S);
+    return 0;
+}
+
+/* One half-step alone (half = 0: dual, 1: primal), for a caller that works
+   between the two (the exchange of halo rows between the bands of an image). */
+int orc_half_step(const orc_problem *P, orc_state *X, int half)
+{
+    int k = P->L - 1, Dz = depth(P);
+    size_t Nk = npix(P) * k;
+    if (Dz > 1 && !X->pz) return -2;
+    orc_steps S;
+    make_steps(P, &S);
+    double *a = (double *)malloc(sizeof(double) * Nk);
+    double *b = (double *)malloc(sizeof(double) * Nk);
+    double *c = (double *)malloc(sizeof(double) * Nk);
+    if (!a || !b || !c) {
+        free(a); free(b); free(c); free_steps(&S); return -1;
+    }
+    if (half == 0) dual_half(P, X, &S, a, b, c);
+    else primal_half(P, X, &S, a);
+    free(a); free(b); free(c);
     free_steps(&S);
     return 0;
 }

@@ -82,6 +82,8 @@ def _load():
         lib.orc_steps_get.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
         lib.orc_pdhg.restype = C.c_int
         lib.orc_pdhg.argtypes = [P, S, C.c_int]
+        lib.orc_half_step.restype = C.c_int
+        lib.orc_half_step.argtypes = [P, S, C.c_int]
         lib.orc_unlift.restype = None
         lib.orc_unlift.argtypes = [P, _dp, _dp]
         lib.orc_monotone_proj.restype = None
@@ -257,6 +259,16 @@ def pdhg(P: Problem, X: State, iters: int) -> State:
     rc = _load().orc_pdhg(P.ref(), C.byref(cs), iters)
     if rc != 0:
         raise MemoryError("oracle pdhg: allocation failed")
+    return X
+
+
+def half_step(P: Problem, X: State, half: int) -> State:
+    """One half-step of the iteration alone: half = 0 the dual step, 1 the
+    primal step (with the extrapolation)."""
+    cs = X._c()
+    rc = _load().orc_half_step(P.ref(), C.byref(cs), half)
+    if rc != 0:
+        raise RuntimeError(f"orc_half_step failed ({rc})")
     return X
 
 

@@ -65,6 +65,12 @@ struct lift_ctx {
     // small problems: whole calls of lift_iterate inside one cluster
     lift::ResidentPlan resident{};
     bool resident_on = true;            // caller's preference (lift_set_resident)
+    // a band of rows of a larger image (lift_create_band): the own rows are
+    // the local pixels [own0, own1), with one halo row above (halo_up) and
+    // below (halo_dn) where the image goes on; torg: the local index, modulo
+    // the primal tile length, that the image's first pixel would have
+    bool band = false;
+    int halo_up = 0, halo_dn = 0, own0 = 0, own1 = 0, torg = 0;
 };
 
 namespace {
@@ -429,6 +435,102 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     return LIFT_OK;
 }
 
+int lift_create_band(const lift_spec *spec, int row0, int row1, void *stream, lift_handle *out)
+{
+    if (!spec || !out) return LIFT_ERR_ARG;
+    *out = nullptr;
+    int rc = validate(spec);
+    if (rc != LIFT_OK) return rc;
+    if (spec->D > 1) return LIFT_ERR_SPEC;               // images only
+    if (row0 < 0 || row1 > spec->H || row0 >= row1) return LIFT_ERR_ARG;
+    const int up = row0 > 0 ? 1 : 0, dn = row1 < spec->H ? 1 : 0;
+    // the local image: the own rows and the halo rows, data from the same rows
+    lift_spec loc = *spec;
+    loc.H = row1 - row0 + up + dn;
+    const size_t first = static_cast<size_t>(row0 - up) * spec->W;
+    if (spec->kind == LIFT_PL_SAMPLED) {
+        if (!spec->cost) return LIFT_ERR_ARG;
+        loc.cost = spec->cost + first * static_cast<size_t>(spec->n_samples);
+    } else {
+        if (!spec->f) return LIFT_ERR_ARG;
+        loc.f = spec->f + first;
+    }
+    rc = lift_create(&loc, stream, out);
+    if (rc != LIFT_OK) return rc;
+    lift_handle h = *out;
+    h->band = true;
+    h->halo_up = up;
+    h->halo_dn = dn;
+    h->own0 = up * spec->W;
+    h->own1 = (up + row1 - row0) * spec->W;
+    const int ppb = h->P.ppb;
+    h->torg = static_cast<int>((static_cast<size_t>(ppb) - first % ppb) % ppb);
+    h->resident_on = false;
+    return LIFT_OK;
+}
+
+int lift_band_halo_bytes(lift_handle h, int which, size_t *bytes)
+{
+    if (!h || !bytes || !h->band) return LIFT_ERR_ARG;
+    const size_t rec = static_cast<size_t>(h->W) * h->k;
+    if (which == LIFT_HALO_PRIMAL) *bytes = 2 * rec * sizeof(float2);
+    else if (which == LIFT_HALO_DUAL) *bytes = rec * sizeof(float4);
+    else return LIFT_ERR_ARG;
+    return LIFT_OK;
+}
+
+// Rows of the local image: the first and last own row, the halo rows.
+static size_t row_rec(lift_handle h, int local_row)
+{
+    return static_cast<size_t>(local_row) * h->W * h->k;
+}
+
+int lift_band_export(lift_handle h, int which, void *dst, int on_host)
+{
+    if (!h || !dst || !h->band) return LIFT_ERR_ARG;
+    const size_t rec = static_cast<size_t>(h->W) * h->k;
+    const cudaMemcpyKind kd = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    char *d = static_cast<char *>(dst);
+    if (which == LIFT_HALO_PRIMAL) {            // first own row, for the band above
+        if (!h->halo_up) return LIFT_ERR_ARG;
+        const size_t o = row_rec(h, h->halo_up);
+        LIFT_CK(cudaMemcpyAsync(d, h->S.x + o, rec * sizeof(float2), kd, h->stream));
+        LIFT_CK(cudaMemcpyAsync(d + rec * sizeof(float2), h->S.xbar + o, rec * sizeof(float2), kd,
+                                h->stream));
+    } else if (which == LIFT_HALO_DUAL) {       // last own row, for the band below
+        if (!h->halo_dn) return LIFT_ERR_ARG;
+        const size_t o = row_rec(h, h->own1 / h->W - 1);
+        LIFT_CK(cudaMemcpyAsync(d, h->S.y + o, rec * sizeof(float4), kd, h->stream));
+    } else {
+        return LIFT_ERR_ARG;
+    }
+    if (on_host) LIFT_CK(cudaStreamSynchronize(h->stream));
+    return LIFT_OK;
+}
+
+int lift_band_import(lift_handle h, int which, const void *src, int on_host)
+{
+    if (!h || !src || !h->band) return LIFT_ERR_ARG;
+    const size_t rec = static_cast<size_t>(h->W) * h->k;
+    const cudaMemcpyKind kd = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const char *s = static_cast<const char *>(src);
+    if (which == LIFT_HALO_PRIMAL) {            // into the halo row below
+        if (!h->halo_dn) return LIFT_ERR_ARG;
+        const size_t o = row_rec(h, h->own1 / h->W);
+        LIFT_CK(cudaMemcpyAsync(h->S.x + o, s, rec * sizeof(float2), kd, h->stream));
+        LIFT_CK(cudaMemcpyAsync(h->S.xbar + o, s + rec * sizeof(float2), rec * sizeof(float2), kd,
+                                h->stream));
+    } else if (which == LIFT_HALO_DUAL) {       // into the halo row above
+        if (!h->halo_up) return LIFT_ERR_ARG;
+        LIFT_CK(cudaMemcpyAsync(h->S.y, s, rec * sizeof(float4), kd, h->stream));
+    } else {
+        return LIFT_ERR_ARG;
+    }
+    // host sources may be reused after return
+    if (on_host) LIFT_CK(cudaStreamSynchronize(h->stream));
+    return LIFT_OK;
+}
+
 void lift_destroy(lift_handle h)
 {
     if (!h) return;
@@ -580,7 +682,7 @@ static int ensure_iter_graph(lift_handle h)
 
 int lift_iterate(lift_handle h, int iters)
 {
-    if (!h || iters < 0) return LIFT_ERR_ARG;
+    if (!h || iters < 0 || h->band) return LIFT_ERR_ARG;
     if (iters > 0 && h->resident.ok && h->resident_on) {
         LIFT_CK(lift::launch_resident(h->P, h->S, iters, h->resident, h->stream));
         return LIFT_OK;
@@ -601,21 +703,26 @@ int lift_iterate(lift_handle h, int iters)
 int lift_dual_step(lift_handle h)
 {
     if (!h) return LIFT_ERR_ARG;
-    LIFT_CK(lift::launch_dual_step(h->P, h->S, h->stream));
+    if (h->band) LIFT_CK(lift::launch_dual_range(h->P, h->S, h->own0, h->own1, h->stream));
+    else LIFT_CK(lift::launch_dual_step(h->P, h->S, h->stream));
     return LIFT_OK;
 }
 
 int lift_primal_step(lift_handle h)
 {
     if (!h) return LIFT_ERR_ARG;
-    LIFT_CK(lift::launch_primal_step(h->P, h->S, h->stream));
+    if (h->band) LIFT_CK(lift::launch_primal_range(h->P, h->S, h->own0, h->own1, h->torg, h->stream));
+    else LIFT_CK(lift::launch_primal_step(h->P, h->S, h->stream));
     return LIFT_OK;
 }
 
 int lift_energy(lift_handle h, double *primal_relaxed, double *dual, double *e_nonconvex)
 {
     if (!h) return LIFT_ERR_ARG;
-    LIFT_CK(lift::launch_energy(h->P, h->S, h->partial, h->dout, h->stream));
+    if (h->band)
+        LIFT_CK(lift::launch_energy_range(h->P, h->S, h->own0, h->own1, h->partial, h->dout, h->stream));
+    else
+        LIFT_CK(lift::launch_energy(h->P, h->S, h->partial, h->dout, h->stream));
     LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
     LIFT_CK(cudaStreamSynchronize(h->stream));
@@ -631,7 +738,7 @@ int lift_energy(lift_handle h, double *primal_relaxed, double *dual, double *e_n
 
 int lift_gap(lift_handle h, double *rel_gap)
 {
-    if (!h || !rel_gap) return LIFT_ERR_ARG;
+    if (!h || !rel_gap || h->band) return LIFT_ERR_ARG;
     double p = 0.0, d = 0.0;
     const int rc = lift_energy(h, &p, &d, nullptr);
     if (rc != LIFT_OK) return rc;
@@ -641,7 +748,7 @@ int lift_gap(lift_handle h, double *rel_gap)
 
 int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done)
 {
-    if (!h || max_iters < 0) return LIFT_ERR_ARG;
+    if (!h || max_iters < 0 || h->band) return LIFT_ERR_ARG;
     if (iters_done) *iters_done = 0;
     if (!(rel_gap_tol > 0.0)) {
         const int rc = lift_iterate(h, max_iters);
@@ -700,12 +807,19 @@ int lift_get_balance(lift_handle h, double *theta)
 int lift_unlift(lift_handle h, float *out, int on_host)
 {
     if (!h || !out) return LIFT_ERR_ARG;
+    // a band unlifts its own rows only
+    LiftParams Pu = h->P;
+    const float2 *x = h->S.x;
+    if (h->band) {
+        Pu.N = h->own1 - h->own0;
+        x += static_cast<size_t>(h->own0) * h->k;
+    }
     if (!on_host) {
-        LIFT_CK(lift::launch_unlift(h->P, h->S.x, out, h->stream));
+        LIFT_CK(lift::launch_unlift(Pu, x, out, h->stream));
         return LIFT_OK;
     }
-    LIFT_CK(lift::launch_unlift(h->P, h->S.x, h->ubuf, h->stream));
-    LIFT_CK(cudaMemcpyAsync(out, h->ubuf, h->N * sizeof(float), cudaMemcpyDeviceToHost,
+    LIFT_CK(lift::launch_unlift(Pu, x, h->ubuf, h->stream));
+    LIFT_CK(cudaMemcpyAsync(out, h->ubuf, Pu.N * sizeof(float), cudaMemcpyDeviceToHost,
                             h->stream));
     LIFT_CK(cudaStreamSynchronize(h->stream));
     return LIFT_OK;
@@ -1371,7 +1485,7 @@ int lift_set_params(lift_handle h, double lambda, double alpha, double nu)
 
 int lift_unrolled_forward(lift_handle h, int iters, int checkpoint_every)
 {
-    if (!h || iters < 1 || checkpoint_every < 1) return LIFT_ERR_ARG;
+    if (!h || iters < 1 || checkpoint_every < 1 || h->band) return LIFT_ERR_ARG;
     if (h->kind == LIFT_PL_SAMPLED || h->P.D > 1) return LIFT_ERR_SPEC;
     const size_t sb = state_stride(h);
     const int nck = (iters + checkpoint_every - 1) / checkpoint_every;

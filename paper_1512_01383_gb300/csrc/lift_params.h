@@ -88,6 +88,15 @@ cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, in
 cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                                cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+// The half-steps on the pixels [p0, p1) of an image.  The primal step's tiles
+// start on the pixels congruent to `origin` modulo its tile length, so the
+// pixel range of one band of a larger image, given the index that the
+// image's first pixel would have, runs its records in the same tile
+// positions (and the same scan order) as the whole image.
+cudaError_t launch_dual_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                              cudaStream_t st);
+cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                int origin, cudaStream_t st);
 
 // One iteration of the merged batch members: the dual step over all their
 // strips (strip_inst: instance of each strip; stage: shared bytes of the
@@ -124,6 +133,10 @@ cudaError_t launch_pl_setup(const LiftParams &P, float *rhat, cudaStream_t st);
 int energy_blocks(const LiftParams &P);
 cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *partial,
                           double *out, cudaStream_t st);
+// The same over the pixels [p0, p1) only (their differences still read the
+// neighbours outside); partial holds (p1 - p0 + 255) / 256 blocks' sums.
+cudaError_t launch_energy_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                double *partial, double *out, cudaStream_t st);
 cudaError_t launch_unlift(const LiftParams &P, const float2 *x, float *out, cudaStream_t st);
 // out[0] = sum |u - u'|^2/tau_u + |s - s'|^2/tau_s, out[1] = sum over the dual
 // records |.|^2/sigma, both in the metric of the theta = 1 steps (the

@@ -645,11 +645,13 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
 // 512^2, L = 20, same registers; on a volume that took 40 -> 46 registers
 // and one block per SM, 117 -> 129 us at 128^3, L = 8, so volumes load them
 // after the scan).
+// The pixels [p0, p1); block b takes the tiles starting at tbase + 2b ppb
+// and tbase + (2b + 1) ppb (tbase <= p0; pixels before p0 are idle).
 template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q,
-                   const float *__restrict__ pz)
+                   const float *__restrict__ pz, int tbase, int p0, int p1)
 {
     __shared__ float2 s_in[kStepThreads];
     __shared__ float2 s_last[kStepThreads / 32];
@@ -670,8 +672,8 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
     };
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-        pix[u] = (2 * (blockIdx.x + P.blk_off) + u) * P.ppb + lp;
-        act[u] = lp < P.ppb && pix[u] < P.N;
+        pix[u] = tbase + (2 * blockIdx.x + u) * P.ppb + lp;
+        act[u] = lp < P.ppb && pix[u] >= p0 && pix[u] < p1;
         o[u] = static_cast<size_t>(pix[u]) * P.k + i;
         d[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         xo[u] = make_float2(0.f, 0.f);
@@ -853,19 +855,39 @@ cudaError_t launch_dual_band(const LiftParams &P0, const LiftState &S, int t0, i
 }
 
 // Primal half-step on the tiles [t0, t1) (two tiles per block).
-cudaError_t launch_primal_band(const LiftParams &P0, const LiftState &S, int t0, int t1,
+cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                                cudaStream_t st)
 {
-    LiftParams P = P0;
-    P.blk_off = t0 / 2;
-    const int nb = (t1 - t0 + 1) / 2;
+    const int p1 = static_cast<int>(std::min<long long>(static_cast<long long>(t1) * P.ppb, P.N));
+    return launch_primal_range(P, S, t0 * P.ppb, p1, 0, st);
+}
+
+cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                int origin, cudaStream_t st)
+{
+    if (p1 <= p0) return cudaSuccess;
+    // the first tile: the largest start <= p0 congruent to origin
+    const int r = ((p0 - origin) % P.ppb + P.ppb) % P.ppb;
+    const int tbase = p0 - r;
+    const int nb = (p1 - tbase + 2 * P.ppb - 1) / (2 * P.ppb);
     if (P.D > 1)
-        primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz);
+        primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz,
+                                                                     tbase, p0, p1);
     else if (P.live != nullptr)
-        primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
+        primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
+                                                                     tbase, p0, p1);
     else
-        primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr);
+        primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
+                                                                      tbase, p0, p1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dual_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                              cudaStream_t st)
+{
+    if (P.D != 1) return cudaErrorInvalidValue;     // images only
+    if (p1 <= p0) return cudaSuccess;
+    return P.kind == 2 ? launch_strips<2>(P, S, p0, p1, st) : launch_strips<0>(P, S, p0, p1, st);
 }
 
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)

@@ -114,11 +114,12 @@ __device__ __forceinline__ float unlift_pixel(const float2 *__restrict__ x, int 
 template <int KIND, bool VOL>
 __global__ void __launch_bounds__(kEnergyThreads)
 energy_kernel(const LiftParams P, const float2 *__restrict__ x, const float4 *__restrict__ y,
-              const float *__restrict__ pz, double *__restrict__ partial)
+              const float *__restrict__ pz, double *__restrict__ partial, int p0, int p1)
 {
-    const int pix = blockIdx.x * kEnergyThreads + threadIdx.x;
+    // the pixels [p0, p1) (a band's own rows; the whole problem otherwise)
+    const int pix = p0 + blockIdx.x * kEnergyThreads + threadIdx.x;
     double eP = 0.0, eD = 0.0, eE = 0.0;
-    if (pix < P.N) {
+    if (pix < p1) {
         const int k = P.k;
         const int row = pix / P.W, col = pix - row * P.W;
         const int yy = VOL ? row % P.H : row;
@@ -245,14 +246,21 @@ int energy_blocks(const LiftParams &P)
 cudaError_t launch_energy(const LiftParams &P, const LiftState &S, double *partial, double *out,
                           cudaStream_t st)
 {
-    const int nb = energy_blocks(P);
+    return launch_energy_range(P, S, 0, P.N, partial, out, st);
+}
+
+cudaError_t launch_energy_range(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                double *partial, double *out, cudaStream_t st)
+{
+    const int nb = (p1 - p0 + kEnergyThreads - 1) / kEnergyThreads;
+    if (nb <= 0) return cudaErrorInvalidValue;
     const bool vol = P.D > 1;
     if (P.kind == 2) {
-        if (vol) energy_kernel<2, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial);
-        else energy_kernel<2, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial);
+        if (vol) energy_kernel<2, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial, p0, p1);
+        else energy_kernel<2, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial, p0, p1);
     } else {
-        if (vol) energy_kernel<0, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial);
-        else energy_kernel<0, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial);
+        if (vol) energy_kernel<0, true><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, S.pz, partial, p0, p1);
+        else energy_kernel<0, false><<<nb, kEnergyThreads, 0, st>>>(P, S.x, S.y, nullptr, partial, p0, p1);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -477,7 +485,8 @@ extern "C" int lift_energy_noalloc(const lift_spec *spec, const void *state, dou
                                                         2 * Nk * sizeof(float2));
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nb = lift::energy_blocks(P);
-    lift::energy_kernel<0, false><<<nb, lift::kEnergyThreads, 0, st>>>(P, x, y, nullptr, scratch);
+    lift::energy_kernel<0, false><<<nb, lift::kEnergyThreads, 0, st>>>(P, x, y, nullptr, scratch, 0,
+                                                                        P.N);
     if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;
     lift::energy_finish_kernel<<<1, lift::kEnergyThreads, 0, st>>>(scratch, nb, out);
     if (cudaGetLastError() != cudaSuccess) return LIFT_ERR_CUDA;

@@ -17,6 +17,7 @@ LIFT_QUAD, LIFT_TRUNC_QUAD, LIFT_PL_SAMPLED, LIFT_PERIODIC_QUAD = 0, 1, 2, 3
 LIFT_OK, LIFT_ERR_SPEC, LIFT_ERR_OOM, LIFT_ERR_CUDA = 0, 1, 2, 3
 LIFT_ERR_NAN, LIFT_ERR_NOT_CONVERGED, LIFT_ERR_ARG, LIFT_ERR_TIMEOUT = 4, 5, 6, 7
 LIFT_MAX_K = 64
+LIFT_HALO_PRIMAL, LIFT_HALO_DUAL = 0, 1
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblift_gb300.so")
 
@@ -32,6 +33,7 @@ EXPORTED = (
     "lift_batch_set_schedule",
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
     "lift_get_balance", "lift_set_resident", "lift_set_bands", "lift_unrolled_generation",
+    "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
 )
 
 
@@ -103,6 +105,10 @@ def load(path: str = LIB_PATH):
         "lift_set_resident": (C.c_int, [vp, C.c_int, ip]),
         "lift_set_bands": (C.c_int, [vp, C.c_int, ip]),
         "lift_unrolled_generation": (C.c_int, [vp, C.POINTER(C.c_ulonglong)]),
+        "lift_create_band": (C.c_int, [C.POINTER(lift_spec), C.c_int, C.c_int, vp, C.POINTER(vp)]),
+        "lift_band_halo_bytes": (C.c_int, [vp, C.c_int, C.POINTER(C.c_size_t)]),
+        "lift_band_export": (C.c_int, [vp, C.c_int, vp, C.c_int]),
+        "lift_band_import": (C.c_int, [vp, C.c_int, vp, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -169,6 +175,30 @@ def lift_reset(h: int) -> None:
 
 def lift_iterate(h: int, iters: int) -> None:
     _check(load().lift_iterate(C.c_void_p(h), iters), "lift_iterate")
+
+
+def lift_create_band(spec: lift_spec, row0: int, row1: int, stream: int | None = None) -> int:
+    h = C.c_void_p()
+    s = current_stream() if stream is None else stream
+    _check(load().lift_create_band(C.byref(spec), row0, row1, C.c_void_p(s), C.byref(h)),
+           "lift_create_band")
+    return h.value
+
+
+def lift_band_halo_bytes(h: int, which: int) -> int:
+    n = C.c_size_t()
+    _check(load().lift_band_halo_bytes(C.c_void_p(h), which, C.byref(n)), "lift_band_halo_bytes")
+    return int(n.value)
+
+
+def lift_band_export(h: int, which: int, dst) -> None:
+    p, on_host = _ptr(dst)
+    _check(load().lift_band_export(C.c_void_p(h), which, C.c_void_p(p), on_host), "lift_band_export")
+
+
+def lift_band_import(h: int, which: int, src) -> None:
+    p, on_host = _ptr(src)
+    _check(load().lift_band_import(C.c_void_p(h), which, C.c_void_p(p), on_host), "lift_band_import")
 
 
 def lift_dual_step(h: int) -> None:
@@ -298,6 +328,29 @@ def make_spec(kind: int, H: int, W: int, L: int, gamma_min: float, gamma_max: fl
                      1 if adaptive_balance else 0, 1 if anisotropic else 0, depth)
 
 
+def state_arrays(h: int, k: int, depth: int = 1) -> dict:
+    """Host copy of a handle's iterate as numpy arrays (the lift_get_state
+    layout: x, xbar, y records, q, and pz on a volume); the pixel count
+    follows from lift_state_bytes (a band handle: its local rows)."""
+    nb = lift_state_bytes(h)
+    per = 32 * k + 4 + (4 * k if depth > 1 else 0)
+    N = nb // per
+    assert N * per == nb
+    buf = np.empty(nb, dtype=np.uint8)
+    lift_get_state(h, buf)
+    f = buf.view(np.float32)
+    o = 0
+    x = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
+    xb = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
+    y = f[o:o + 4 * N * k].reshape(N, k, 4); o += 4 * N * k
+    q = f[o:o + N]; o += N
+    st = {"u": x[..., 0], "s": x[..., 1], "ubar": xb[..., 0], "sbar": xb[..., 1],
+          "v": y[..., 0], "z": y[..., 1], "px": y[..., 2], "py": y[..., 3], "q": q}
+    if depth > 1:
+        st["pz"] = f[o:o + N * k].reshape(N, k)
+    return st
+
+
 class Solver:
     """A lifted problem on the GPU: ``Solver(kind, H, W, L, ...)``; depth > 1
     makes it a depth x H x W volume."""
@@ -367,21 +420,7 @@ class Solver:
 
     def state(self) -> dict:
         """Host copy of the iterate as numpy arrays (layout of include/lift.h)."""
-        nb = lift_state_bytes(self.h)
-        buf = np.empty(nb, dtype=np.uint8)
-        lift_get_state(self.h, buf)
-        N, k = self.N, self.k
-        f = buf.view(np.float32)
-        o = 0
-        x = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
-        xb = f[o:o + 2 * N * k].reshape(N, k, 2); o += 2 * N * k
-        y = f[o:o + 4 * N * k].reshape(N, k, 4); o += 4 * N * k
-        q = f[o:o + N]; o += N
-        st = {"u": x[..., 0], "s": x[..., 1], "ubar": xb[..., 0], "sbar": xb[..., 1],
-              "v": y[..., 0], "z": y[..., 1], "px": y[..., 2], "py": y[..., 3], "q": q}
-        if self.D > 1:
-            st["pz"] = f[o:o + N * k].reshape(N, k)
-        return st
+        return state_arrays(self.h, self.k, self.D)
 
     def set_state(self, st: dict):
         N, k = self.N, self.k
