@@ -52,9 +52,23 @@ WORKLOAD = ("truncated-quadratic denoising 512x512, L=20 (k=19), alpha=25 nu=0.1
 #   primal step: read primal 8k + dual 16k + q 4, write primal 8k + xbar 8k = 40k + 4
 DUAL_BYTES_PER_PIX = 40 * K_INT + 12
 PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
-# DRAM bytes per dual-step launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum); None while no capture of the current kernel exists.
+# DRAM bytes of one dual-step launch at this workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel sources
+# whose SHA-256 (of the files below, in this order) is DUAL_TRAFFIC_SRC; with
+# any other source the bench reports no traffic figure.
 DUAL_TRAFFIC_NCU = None
+DUAL_TRAFFIC_SRC = None
+DUAL_KERNEL_FILES = ("pdhg_step.cu", "lift_device.cuh", "lift_bulk.cuh", "lift_params.h",
+                     "lift_tile.cuh")
+
+
+def dual_kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in DUAL_KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_1512_01383_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -486,6 +500,94 @@ def cpu_sample_all_cores(f: np.ndarray, side: int, iters: int, reps: int = 1,
     return n, out
 
 
+# ---------------------------------------------------------------------------
+# Error against the FP64 oracle, for every configuration: the FP32 GPU path
+# and the oracle run the same problem (a crop or small instance of each
+# configuration's inputs, same parameters and balance) for the same fixed
+# number of iterations; the unlifted images and the three energies are
+# compared.  Part of the CPU-baseline leg (the oracle runs in spawned workers).
+# ---------------------------------------------------------------------------
+def error_cases():
+    """(name, problem description, iterations) per configuration."""
+    from paper_1512_01383_gb300 import synth
+    cases = []
+    f = np.ascontiguousarray(make_input(0)[:192, :192])
+    for Lx in (5, 10, 20):
+        cases.append((f"truncated_512_L{Lx}", dict(kind=1, H=192, W=192, L=Lx, gmin=0.0, gmax=1.0,
+                      lam=LAM, alpha=ALPHA, nu=NU, f=f, theta=float((Lx - 1) ** 2)), 100))
+    fr = synth.as_f32(synth.gaussian_blobs(64, 64, synth.BASE_SEED))
+    cases.append(("rof_64x64_L2", dict(kind=0, H=64, W=64, L=2, gmin=0.0, gmax=1.0, lam=0.2,
+                                       alpha=1.0, nu=0.0, f=fr, theta=1.0), 2000))
+    cost = synth.as_f32(synth.stereo_cost(480, 640, synth.BASE_SEED + 3, ndisp=65)[0][:96, :96])
+    for Lx in (8, 16, 32):
+        cases.append((f"stereo_640x480_L{Lx}", dict(kind=2, H=96, W=96, L=Lx, gmin=0.0, gmax=64.0,
+                      lam=0.05, cost=cost, smin=0.0, smax=64.0, theta=1.0), 100))
+    w = synth.as_f32(synth.wrapped_phase(512, 512, synth.BASE_SEED + 5)[0][:128, :128])
+    cases.append(("phase_unwrapping_512_L8", dict(kind=3, H=128, W=128, L=8, gmin=0.0,
+                  gmax=float(4 * np.pi), lam=0.2, alpha=1.0, nu=float(2 * np.pi), f=w,
+                  theta=1.0), 100))
+    fv = synth.as_f32(synth.voronoi_ramps_3d(128, 128, 128, synth.BASE_SEED + 7)[0][:24, :24, :24])
+    cases.append(("volume_128cubed_L8", dict(kind=1, H=24, W=24, D=24, L=8, gmin=0.0, gmax=1.0,
+                  lam=LAM, alpha=ALPHA, nu=NU, f=fv, theta=1.0), 50))
+    fd = synth.as_f32(synth.voronoi_ramps(256, 256, synth.BASE_SEED + 4)[0][:96, :96])
+    cases.append(("differentiable_256_L16", dict(kind=1, H=96, W=96, L=16, gmin=0.0, gmax=1.0,
+                  lam=0.25, alpha=25.0, nu=0.1, f=fd, theta=1.0), 100))
+    sd, Lb = synth.batch_instances(64, synth.BASE_SEED + 2, 128, 1024)[0]
+    fb = synth.as_f32(synth.voronoi_ramps(sd, sd, synth.BASE_SEED + 2)[0][:128, :128])
+    cases.append((f"batch_instance0_L{Lb}", dict(kind=1, H=128, W=128, L=Lb, gmin=0.0, gmax=1.0,
+                  lam=LAM, alpha=ALPHA, nu=NU, f=fb, theta=float((Lb - 1) ** 2)), 100))
+    lab = np.linspace(0.0, 1.0, 8)
+    fl = np.ascontiguousarray(make_input(0)[:128, :128], dtype=np.float64)
+    cl = synth.as_f32(np.minimum(ALPHA * (lab[None, None, :] - fl[:, :, None]) ** 2, NU))
+    cases.append(("baseline_lifting_512_L8", dict(kind=2, H=128, W=128, L=8, gmin=0.0, gmax=1.0,
+                  lam=LAM, cost=cl, smin=0.0, smax=1.0, theta=1.0), 100))
+    return cases
+
+
+def _oracle_case(job):
+    """One configuration's oracle run (in a spawned worker): unlifted image
+    and the three energies after `iters` iterations."""
+    c, iters = job
+    import oracle as O
+    kinds = {0: O.QUAD, 1: O.TRUNC, 2: O.PL, 3: O.PERIODIC}
+    P = O.Problem(kinds[c["kind"]], c["H"], c["W"], c["L"], c["gmin"], c["gmax"], lam=c["lam"],
+                  alpha=c.get("alpha", 1.0), nu=c.get("nu", 0.0),
+                  f=None if c.get("f") is None else c["f"].astype(np.float64),
+                  cost=None if c.get("cost") is None else c["cost"].astype(np.float64),
+                  smin=c.get("smin", 0.0), smax=c.get("smax", 1.0), theta=c["theta"],
+                  D=c.get("D", 1))
+    X = O.State(P)
+    O.pdhg(P, X, iters)
+    return O.unlift(P, X.u), O.energy(P, X)
+
+
+def fp64_errors(G, torch, dev, pool):
+    """Per configuration: max |u~_GPU - u~_oracle| / (label range) and the
+    relative errors max(|.|, 1)-normalised of P, D and E_nc."""
+    cases = error_cases()
+    pending = pool.map_async(_oracle_case, [(c, it) for _, c, it in cases], chunksize=1)
+    gpu = []
+    for name, c, iters in cases:
+        kw = dict(f=None if c.get("f") is None else torch.from_numpy(c["f"]).to(dev),
+                  cost=None if c.get("cost") is None else torch.from_numpy(c["cost"]).to(dev),
+                  sample_min=c.get("smin", 0.0), sample_max=c.get("smax", 1.0),
+                  step_balance=c["theta"], depth=c.get("D", 1))
+        with G.Solver(c["kind"], c["H"], c["W"], c["L"], c["gmin"], c["gmax"], c["lam"],
+                      c.get("alpha", 1.0), c.get("nu", 0.0), **kw) as s:
+            s.iterate(iters)
+            gpu.append((s.unlift().reshape(-1).astype(np.float64), s.energy()))
+    out = {}
+    for (name, c, iters), (ug, eg), (uo, eo) in zip(cases, gpu, pending.get(timeout=900)):
+        rng = c["gmax"] - c["gmin"]
+        rel = [abs(a - b) / max(abs(b), 1.0) for a, b in zip(eg, eo)]
+        shape = "x".join(str(v) for v in ([c["D"]] if c.get("D", 1) > 1 else []) + [c["H"], c["W"]])
+        out[name] = {"u_maxabs_over_label_range": float(np.abs(ug - uo).max() / rng),
+                     "P_rel": rel[0], "D_rel": rel[1], "E_nc_rel": rel[2],
+                     "instance": f"{shape} of the configuration's inputs, L={c['L']}, "
+                                 f"{iters} iterations"}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -734,7 +836,11 @@ def main():
         batch["small_instances"] = run_batch(G, torch, stream, dev, n=256, smin=32, smax=128)
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(_host_cores(), len(error_cases()))) as pool:
+            errors = fp64_errors(G, torch, dev, pool)
         side, iters = 192, 60
         v1, dt = cpu_sample(f, side, iters)
         n, [(vn, wall)] = cpu_sample_all_cores(f, side, iters)
@@ -743,7 +849,8 @@ def main():
                          f"own {side}x{side} crop, L={L}, {iters} iterations + energy + unlift "
                          f"({wall:.1f} s wall)",
                "single_core": {"value": v1, "sample": f"one {side}x{side} crop, same iterations "
-                                                      f"({dt:.1f} s)"}}
+                                                      f"({dt:.1f} s)"},
+               "fp64_error": errors}
 
     if rank == 0:
         line = {
@@ -756,7 +863,11 @@ def main():
                        "l2": "inputs larger than L2 (160 MB state, 403 MB per iteration)"},
             "roofline": {"bound": "hbm", "kernel": "dual_strip_kernel (dual step)", "achieved": dual_gbs,
                          "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                         "frac": dual_gbs / peak, "traffic": DUAL_TRAFFIC_NCU,
+                         "frac": dual_gbs / peak,
+                         "traffic": DUAL_TRAFFIC_NCU if dual_kernel_hash() == DUAL_TRAFFIC_SRC else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                           "dual_strip_kernel launch at this workload, for the "
+                                           "kernel source hash DUAL_TRAFFIC_SRC",
                          "algorithmic_bytes_per_launch": DUAL_BYTES_PER_PIX * H * W,
                          "launch_ms": dual_ms,
                          "primal_step": {"achieved": primal_gbs, "frac": primal_gbs / peak,
@@ -776,6 +887,9 @@ def main():
                                        "algorithmic_bytes_per_iteration":
                                            (DUAL_BYTES_PER_PIX + PRIMAL_BYTES_PER_PIX) * H * W}},
             "cpu_baseline": cpu,
+            # the FP32 GPU path against the FP64 oracle, per configuration
+            # (measured in the CPU-baseline leg, which runs the oracle)
+            "fp64_error": errors,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
                     "d2h_bytes_per_step": H * W * 4 + 24},
             # per iteration one dual and one primal launch per band, then the

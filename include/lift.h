@@ -49,6 +49,10 @@ extern "C" {
                                       (reported by the next lift_energy /
                                       lift_gap / lift_solve check)          */
 
+/* lift_cuda_error: the name of the CUDA error (as cudaGetErrorName) behind
+ * the calling thread's most recent LIFT_ERR_CUDA, or "no error". */
+const char *lift_cuda_error(void);
+
 /* Largest supported number of label intervals k = L-1. */
 #define LIFT_MAX_K 64
 

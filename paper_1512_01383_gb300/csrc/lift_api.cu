@@ -53,6 +53,7 @@ struct lift_ctx {
     // banded graph: per band a stream for the dual and one for the primal
     // half-steps, ordered by events (see ensure_iter_graph)
     int bands_req = 0;                  // lift_set_bands: 0 = automatic
+    long long l2_bytes = 0;             // the device's L2 size (the automatic band count)
     cudaStream_t band_s[2 * kMaxBands] = {};
     cudaEvent_t band_e[2 * kMaxBands + 1] = {};
     // adaptive primal/dual balance (lift_solve)
@@ -75,10 +76,16 @@ struct lift_ctx {
 
 namespace {
 
+// The CUDA error behind the calling thread's last LIFT_ERR_CUDA.
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 #define LIFT_CK(call)                                  \
     do {                                               \
         cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return LIFT_ERR_CUDA;   \
+        if (e_ != cudaSuccess) {                       \
+            g_last_cuda_error = e_;                    \
+            return LIFT_ERR_CUDA;                      \
+        }                                              \
     } while (0)
 
 int dev_alloc(void **p, size_t bytes)
@@ -428,6 +435,14 @@ int lift_create(const lift_spec *spec, void *stream, lift_handle *out)
     rc = lift_reset(h);
     if (rc != LIFT_OK) { free_ctx(h); return rc; }
     lift::plan_resident(h->P, h->resident);
+    {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
+            h->l2_bytes = l2;
+        else
+            cudaGetLastError();
+    }
     // host-side vectors die with this scope: finish the uploads first
     CUDA_OR_FAIL(cudaStreamSynchronize(h->stream));
 #undef CUDA_OR_FAIL
@@ -580,13 +595,25 @@ static void drop_iter_graph(lift_handle h)
 
 static int step_tiles(lift_handle h) { return (h->P.N + h->P.ppb - 1) / h->P.ppb; }
 
-// Number of bands of the iteration graph: 4 by default for problems of at
-// least 4096 tiles, fewer (down to 1) while a band would hold less than the
-// largest neighbour offset (a row of an image, a slice of a volume), so that
-// every halo value lies in the same or an adjacent band.
+// Number of bands of the iteration graph.  By default 4 for problems of at
+// least 4096 tiles, where the dual steps of some bands overlap the primal
+// steps of others; but 1 where the dual step runs in strips and the state
+// exceeds three quarters of L2: there both half-steps stream from DRAM at
+// near its bandwidth and overlapping them only makes them contend (512^2,
+// L = 20, 160 MB: 74 us per iteration in one band, 87 in four; at L = 10,
+// 76 MB, four bands gain 6 %).  Fewer bands (down to 1) while a band would
+// hold less than the largest neighbour offset (a row of an image, a slice of
+// a volume), so that every halo value lies in the same or an adjacent band.
 static int bands_used(lift_handle h)
 {
-    int B = h->bands_req > 0 ? std::min(h->bands_req, kMaxBands) : (step_tiles(h) >= 4096 ? 4 : 1);
+    int B = 1;
+    if (h->bands_req > 0) {
+        B = std::min(h->bands_req, kMaxBands);
+    } else if (step_tiles(h) >= 4096) {
+        const bool strips = h->P.D == 1 && h->kind != LIFT_PL_SAMPLED;
+        const long long state = static_cast<long long>(lift_state_bytes(h));
+        B = strips && h->l2_bytes > 0 && 4 * state > 3 * h->l2_bytes ? 1 : 4;
+    }
     const long long span = h->P.D > 1 ? h->P.HW : h->P.W;
     // boundaries fall on even tiles, so a band holds at least T/B - 2 tiles
     while (B > 1 && (static_cast<long long>(step_tiles(h) / B - 2) * h->P.ppb <= span)) --B;
@@ -703,7 +730,7 @@ int lift_iterate(lift_handle h, int iters)
 int lift_dual_step(lift_handle h)
 {
     if (!h) return LIFT_ERR_ARG;
-    if (h->band) LIFT_CK(lift::launch_dual_range(h->P, h->S, h->own0, h->own1, h->stream));
+    if (h->band) LIFT_CK(lift::launch_dual_range(h->P, h->S, h->own0, h->own1, h->torg, h->stream));
     else LIFT_CK(lift::launch_dual_step(h->P, h->S, h->stream));
     return LIFT_OK;
 }
@@ -880,6 +907,11 @@ int lift_envelope(lift_handle h, const int *pix, const int *interval, const floa
     if (!h || n < 0 || (n > 0 && (!pix || !interval || !t || !out))) return LIFT_ERR_ARG;
     LIFT_CK(lift::launch_envelope(h->P, pix, interval, t, out, n, h->stream));
     return LIFT_OK;
+}
+
+const char *lift_cuda_error(void)
+{
+    return g_last_cuda_error == cudaSuccess ? "no error" : cudaGetErrorName(g_last_cuda_error);
 }
 
 const char *lift_strerror(int code)

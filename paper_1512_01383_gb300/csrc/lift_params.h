@@ -88,13 +88,14 @@ cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, in
 cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                                cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
-// The half-steps on the pixels [p0, p1) of an image.  The primal step's tiles
-// start on the pixels congruent to `origin` modulo its tile length, so the
+// The half-steps on the pixels [p0, p1) of an image.  Tiles (the primal
+// step's, and the dual step's of sampled costs) start on the pixels
+// congruent to `origin` modulo the tile length, so the
 // pixel range of one band of a larger image, given the index that the
 // image's first pixel would have, runs its records in the same tile
 // positions (and the same scan order) as the whole image.
 cudaError_t launch_dual_range(const LiftParams &P, const LiftState &S, int p0, int p1,
-                              cudaStream_t st);
+                              int origin, cudaStream_t st);
 cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0, int p1,
                                 int origin, cudaStream_t st);
 

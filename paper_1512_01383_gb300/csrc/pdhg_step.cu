@@ -37,6 +37,7 @@
 #include "lift_tile.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace lift {
 
@@ -86,17 +87,18 @@ __device__ __forceinline__ SegScan2 block_segmented_scan2(float2 val, int seg, i
 // the batched kernels below.  VOL: a D x H x W volume, whose p_i has a third
 // component in pz (Sec. 4 on the d = 3 grid); images take VOL = false and
 // never touch pz.
+// The tile's pixels start at pbase; only those in [p0, p1) are updated.
 template <int KIND, int THREADS, bool VOL = false>
 __device__ __forceinline__ void dual_tile(const LiftParams &P, const float2 *__restrict__ xbar,
                                           float4 *__restrict__ y, float *__restrict__ q,
-                                          int tile, float *s_in, float *s_last,
+                                          int pbase, int p0, int p1, float *s_in, float *s_last,
                                           float *__restrict__ pz = nullptr)
 {
     const int tid = threadIdx.x;
     int lp, i;
     split_thread(P, tid, lp, i);
-    const int pix = tile * P.ppb + lp;
-    const bool active = lp < P.ppb && pix < P.N;
+    const int pix = pbase + lp;
+    const bool active = lp < P.ppb && pix >= p0 && pix < p1;
     const size_t o = static_cast<size_t>(pix) * P.k + i;
 
     float2 xb = make_float2(0.0f, 0.0f);
@@ -198,17 +200,21 @@ __device__ __forceinline__ void primal_tile(const LiftParams &P, float2 *__restr
     xbar[o] = make_float2(2.0f * un - xo.x, 2.0f * sn - xo.y);
 }
 
-// The dual step of a volume: one tile per block.  LIVE: a batch member,
-// whose blocks return while its live flag is 0.
+// The dual step in tiles, one per block (volumes, and sampled costs on
+// images, whose hull walks read per-pixel tables that record-per-thread
+// tiles read coalesced).  Block b takes the tile starting at tbase + b ppb;
+// only the pixels [p0, p1) are updated.  LIVE: a batch member, whose blocks
+// return while its live flag is 0.
 template <int KIND, bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 dual_step_kernel(const LiftParams P, const float2 *__restrict__ xbar, float4 *__restrict__ y,
-                 float *__restrict__ q, float *__restrict__ pz)
+                 float *__restrict__ q, float *__restrict__ pz, int tbase, int p0, int p1)
 {
     __shared__ float s_in[kStepThreads];
     __shared__ float s_last[kStepThreads / 32];
     if (LIVE && *P.live == 0) return;
-    dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, blockIdx.x + P.blk_off, s_in, s_last, pz);
+    dual_tile<KIND, kStepThreads, VOL>(P, xbar, y, q, tbase + blockIdx.x * P.ppb, p0, p1, s_in,
+                                       s_last, pz);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,14 +754,54 @@ batch_primal_kernel(const InstDesc *__restrict__ D, const int *__restrict__ tile
                          s_last);
 }
 
-// The dynamic shared-memory limit is a per-device attribute of a kernel: set
-// it to what the strips need before a launch.
+// Per device: the SM count, and per strip-kernel shape the CTAs that fit on
+// an SM at once, with the kernel's dynamic shared-memory limit raised to
+// what the shape needs.  Looked up once per (device, kernel, shape) and kept,
+// so a launch costs no device queries (direct launches of small problems are
+// host-bound otherwise).
+constexpr int kStripSmemCap = 200 * 1024;   // above every strip shape's need
+
+struct StripOcc {
+    int dev = -1, kind = -1, threads = 0, bytes = 0, per_sm = 0, sms = 0;
+};
+
 template <int KIND>
-static cudaError_t strip_attr(int bytes)
+static cudaError_t strip_occupancy(int threads, int bytes, int *ctas)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(dual_strip_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                bytes);
+    static std::mutex mu;
+    static StripOcc cache[32];
+    static int next = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const StripOcc &c : cache)
+            if (c.dev == dev && c.kind == KIND && c.threads == threads && c.bytes == bytes) {
+                *ctas = c.per_sm * c.sms;
+                return cudaSuccess;
+            }
+    }
+    StripOcc c;
+    c.dev = dev;
+    c.kind = KIND;
+    c.threads = threads;
+    c.bytes = bytes;
+    e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+    // one cap for every shape (each launch still asks for its own bytes): a
+    // cap set to one shape's size would refuse a larger shape cached earlier
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(dual_strip_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kStripSmemCap);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, dual_strip_kernel<KIND>,
+                                                          threads, bytes);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[next] = c;
+    next = (next + 1) % 32;
+    *ctas = c.per_sm * c.sms;
+    return cudaSuccess;
 }
 
 template <int THREADS>
@@ -774,7 +820,9 @@ cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *ti
     if (nstrips > 0) {
         // every strip has kBatchStripThreads threads; stage: the largest staged records
         const int bytes = stage + 64 * 16 + (kBatchStripThreads / 32) * 96 * 16;
-        cudaError_t e = strip_attr<0>(bytes);
+        if (bytes > kStripSmemCap) return cudaErrorInvalidValue;
+        int resident = 0;
+        cudaError_t e = strip_occupancy<0>(kBatchStripThreads, bytes, &resident);
         if (e != cudaSuccess) return e;
         LiftParams none{};
         dual_strip_kernel<0><<<nstrips, kBatchStripThreads, bytes, st>>>(none, nullptr, nullptr, nullptr,
@@ -819,39 +867,45 @@ static cudaError_t launch_strips(const LiftParams &P, const LiftState &S, int p0
     if (nstrips <= 0) return cudaSuccess;
     const int threads = spp << strip_tshift(P.k);
     const int bytes = strip_smem(spp, P.k, threads).bytes;
-    cudaError_t e = strip_attr<KIND>(bytes);
-    if (e != cudaSuccess) return e;
+    if (bytes > kStripSmemCap) return cudaErrorInvalidValue;
     // CTAs resident at once: a CTA prefetches the strip of the CTA that will
     // take its place
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dual_strip_kernel<KIND>, threads, bytes);
+    int resident = 0;
+    const cudaError_t e = strip_occupancy<KIND>(threads, bytes, &resident);
     if (e != cudaSuccess) return e;
     dual_strip_kernel<KIND><<<nstrips, threads, bytes, st>>>(P, S.xbar, S.y, S.q, p0, p1, nullptr,
-                                                            nullptr, nullptr, P.err, per_sm * sms);
+                                                            nullptr, nullptr, P.err, resident);
     return cudaGetLastError();
 }
 
-// Dual half-step on the tiles [t0, t1): images in strips (the pixels of those
-// tiles), volumes in tiles.
-cudaError_t launch_dual_band(const LiftParams &P0, const LiftState &S, int t0, int t1,
+// Dual half-step in tiles over [p0, p1), tiles aligned to `origin`.
+static cudaError_t launch_dual_tiles(const LiftParams &P, const LiftState &S, int p0, int p1,
+                                     int origin, cudaStream_t st)
+{
+    if (p1 <= p0) return cudaSuccess;
+    const int r = ((p0 - origin) % P.ppb + P.ppb) % P.ppb;
+    const int tbase = p0 - r;
+    const int nb = (p1 - tbase + P.ppb - 1) / P.ppb;
+    const bool vol = P.D > 1, live = P.live != nullptr;
+    if (P.kind == 2) {
+        if (vol) dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz, tbase, p0, p1);
+        else if (live) dual_step_kernel<2, false, true><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr, tbase, p0, p1);
+        else dual_step_kernel<2, false, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, nullptr, tbase, p0, p1);
+    } else {
+        dual_step_kernel<0, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz, tbase, p0, p1);
+    }
+    return cudaGetLastError();
+}
+
+// Dual half-step on the tiles [t0, t1): quadratic kinds on images in strips
+// (the pixels of those tiles), sampled costs and volumes in tiles.
+cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                              cudaStream_t st)
 {
-    LiftParams P = P0;
-    if (P.D == 1) {
-        const int p0 = t0 * P.ppb;
-        const int p1 = static_cast<int>(std::min<long long>(static_cast<long long>(t1) * P.ppb, P.N));
-        return P.kind == 2 ? launch_strips<2>(P, S, p0, p1, st) : launch_strips<0>(P, S, p0, p1, st);
-    }
-    P.blk_off = t0;
-    const int nb = t1 - t0;
-    if (P.kind == 2)
-        dual_step_kernel<2, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-    else
-        dual_step_kernel<0, true, false><<<nb, kStepThreads, 0, st>>>(P, S.xbar, S.y, S.q, S.pz);
-    return cudaGetLastError();
+    const int p0 = t0 * P.ppb;
+    const int p1 = static_cast<int>(std::min<long long>(static_cast<long long>(t1) * P.ppb, P.N));
+    if (P.D == 1 && P.kind != 2) return launch_strips<0>(P, S, p0, p1, st);
+    return launch_dual_tiles(P, S, p0, p1, 0, st);
 }
 
 // Primal half-step on the tiles [t0, t1) (two tiles per block).
@@ -883,11 +937,12 @@ cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0,
 }
 
 cudaError_t launch_dual_range(const LiftParams &P, const LiftState &S, int p0, int p1,
-                              cudaStream_t st)
+                              int origin, cudaStream_t st)
 {
     if (P.D != 1) return cudaErrorInvalidValue;     // images only
     if (p1 <= p0) return cudaSuccess;
-    return P.kind == 2 ? launch_strips<2>(P, S, p0, p1, st) : launch_strips<0>(P, S, p0, p1, st);
+    if (P.kind != 2) return launch_strips<0>(P, S, p0, p1, st);
+    return launch_dual_tiles(P, S, p0, p1, origin, st);
 }
 
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st)

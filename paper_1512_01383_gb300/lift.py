@@ -34,6 +34,7 @@ EXPORTED = (
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
     "lift_get_balance", "lift_set_resident", "lift_set_bands", "lift_unrolled_generation",
     "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
+    "lift_cuda_error",
 )
 
 
@@ -52,7 +53,10 @@ class lift_spec(C.Structure):
 class LiftError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} (code {code})")
+        detail = ""
+        if code == LIFT_ERR_CUDA:
+            detail = f" [{load().lift_cuda_error().decode()}]"
+        super().__init__(f"{where}: {strerror(code)} (code {code}){detail}")
 
 
 _lib = None
@@ -109,6 +113,7 @@ def load(path: str = LIB_PATH):
         "lift_band_halo_bytes": (C.c_int, [vp, C.c_int, C.POINTER(C.c_size_t)]),
         "lift_band_export": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "lift_band_import": (C.c_int, [vp, C.c_int, vp, C.c_int]),
+        "lift_cuda_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
