@@ -616,6 +616,8 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     case 6: tail = strip_chunk<PK, 6>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
     case 7: tail = strip_chunk<PK, 7>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
     case 8: tail = strip_chunk<PK, 8>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 9: tail = strip_chunk<PK, 9>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
+    case 10: tail = strip_chunk<PK, 10>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, tshift, act, hasR, hasD, fv, stp.z, lane); break;
     default:
         tail = strip_chunk_any<PK>(P, &sP, sY, sX, sD, sIC, R, pix0, t, lo, c, tshift, act, hasR, hasD, fv,
                                    stp.z, lane);
@@ -849,12 +851,15 @@ static inline int step_blocks(const LiftParams &P)
 }
 
 // Pixels per strip for k records per pixel on a single problem: 256 / T
-// threads' worth, fewer (down to 32) while the staged records exceed 40 KB,
-// so that four CTAs fit on an SM.
+// threads' worth, fewer (in steps of one warp's pixels, down to one warp)
+// while the staged records exceed kStripStage bytes.
+constexpr int kStripStage = 20 * 1024;
+
 static int strip_spp(int k)
 {
-    int spp = 256 >> strip_tshift(k);
-    while (spp > 32 && strip_smem(spp, k, spp << strip_tshift(k)).stage > 40 * 1024) spp -= 32;
+    const int ts = strip_tshift(k), step = 32 >> ts;
+    int spp = 256 >> ts;
+    while (spp > step && strip_smem(spp, k, spp << ts).stage > kStripStage) spp -= step;
     return spp;
 }
 
