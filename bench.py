@@ -196,6 +196,7 @@ def run_batch(G, torch, stream, dev, n=64, smin=128, smax=1024, iters=100, reps=
     try:
         G.lift_batch_autotune(b, 3)
         threads, big_tiles, n_big = G.lift_batch_schedule(b)
+        nfork = G.lift_batch_streams(b)
         G.lift_batch_iterate(b, iters)           # capture + warm-up
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -226,7 +227,7 @@ def run_batch(G, torch, stream, dev, n=64, smin=128, smax=1024, iters=100, reps=
     return {"instances": n, "side_range": [smin, smax], "pixels": sum(sd * sd for sd, _ in inst),
             "pix_k": sum(sd * sd * (Lj - 1) for sd, Lj in inst), "iters_per_launch": iters,
             "schedule": {"merged_tile_threads": threads, "big_tiles": big_tiles,
-                         "instances_on_single_kernels": n_big},
+                         "instances_on_single_kernels": n_big, "streams_of_big_instances": nfork},
             "value": units / (ms_batch * 1e-3) / 1e9, "unit": UNIT,
             "loop_of_single_solves": units / (ms_loop * 1e-3) / 1e9,
             "speedup_vs_loop": ms_loop / ms_batch,

@@ -394,20 +394,29 @@ int lift_batch_unlift(lift_batch b, int i, float *out, int on_host);
 /* lift_batch_get_state: state image of instance i (layout of lift_get_state). */
 int lift_batch_get_state(lift_batch b, int i, void *dst, size_t bytes, int on_host);
 
-/* lift_batch_autotune: time `iters` iterations for each tile width of the
- * merged launch (128, 256, 512 threads) and each big-instance threshold (none,
- * 1, 2 or 4 full waves of 256-thread tiles) on this batch and keep the
- * fastest (*threads_chosen, may be NULL).  Resets every iterate to zero. */
+/* lift_batch_autotune: time `iters` iterations, as the captured graph that
+ * lift_batch_iterate replays, for each tile width of the merged primal
+ * launch (128, 256, 512 threads), each big-instance threshold (none, 1, 2 or
+ * 4 full waves of 256-thread tiles) and each number of streams that the big
+ * instances share (1, 2, 4: several big instances run at once) on this
+ * batch, and keep the fastest (*threads_chosen, may be NULL).  Resets every
+ * iterate to zero. */
 int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen);
 
+/* lift_batch_streams: set (set = 1..4; 0 leaves it) and read (*n, may be
+ * NULL) the number of streams that the big instances share in a captured
+ * interval.  LIFT_ERR_ARG for other values. */
+int lift_batch_streams(lift_batch b, int set, int *n);
+
 /* lift_batch_set_schedule: set the schedule by hand: tile width of the
- * merged launch (128, 256 or 512 threads, at least k of every instance left
- * in it, else LIFT_ERR_ARG and the schedule is unchanged) and the
- * big-instance threshold in 256-thread tiles (0: every instance merged; 1:
- * every instance on the single-instance kernels).  The iterates are kept.
- * With 256-thread tiles every instance follows its single handle's map
- * bitwise; other widths change only the association order of the per-pixel
- * sums over intervals. */
+ * merged primal launch (128, 256 or 512 threads, at least k of every
+ * instance left in it, else LIFT_ERR_ARG and the schedule is unchanged) and
+ * the big-instance threshold in 256-thread tiles (0: every instance merged;
+ * 1: every instance on the single-instance kernels).  The iterates are kept.
+ * The merged dual steps run each instance in its single handle's strips.
+ * With 256-thread primal tiles every instance follows its single handle's
+ * map bitwise; other widths change only the association order of the
+ * per-pixel sums over intervals in the primal step. */
 int lift_batch_set_schedule(lift_batch b, int threads, int big_tiles);
 
 /* lift_batch_schedule: the current schedule: tile width of the merged

@@ -945,6 +945,7 @@ struct lift_batch_ctx {
     bool own_stream = false;
     int n = 0, kind = 0, check_every = 100, threads = lift::kStepThreads;
     int big_tiles = 0;                  // 0: every instance shares the merged launch
+    int nfork = 4;                      // streams the big instances share in a captured interval
     int wave = 1;                       // 256-thread tiles resident on the whole GPU
     std::vector<LiftParams> P;          // host copies (device pointers filled in)
     std::vector<LiftState> S;
@@ -954,9 +955,9 @@ struct lift_batch_ctx {
     void *arena = nullptr;              // all per-instance device arrays
     lift::InstDesc *desc = nullptr;     // device [n]
     int *tile_inst = nullptr;           // device [total tiles]: instance of each tile
-    int *strip_inst = nullptr;          // device [total strips]: instance of each dual strip
+    int *strip_inst = nullptr;          // device: instance of each dual strip, group by group
     int total_tiles = 0, total_strips = 0;
-    int strip_stage = 0;                // shared bytes of the largest merged strip stage
+    std::vector<lift::StripGroup> groups;   // the merged members' dual strips by CTA shape
     int *err = nullptr;                 // device: set by a kernel whose bounded wait gave up
     int *live = nullptr;                // device [n]: 1 = still iterating
     std::vector<int> live_h;
@@ -1006,10 +1007,14 @@ void free_batch(lift_batch b)
 int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 {
     std::vector<lift::InstDesc> d(b->n);
-    std::vector<int> ti, si;
-    int t0 = 0, stage = 0;
+    std::vector<int> ti;
+    int t0 = 0;
     b->big.clear();
     b->Pbig.clear();
+    // merged members' dual strips, grouped by the CTA threads of their shape
+    std::vector<int> gthreads;
+    std::vector<std::vector<int>> gstrips;
+    std::vector<int> gbytes;
     for (int j = 0; j < b->n; ++j) {
         LiftParams Ps = b->P[j];
         Ps.ppb = lift::kStepThreads / Ps.k;
@@ -1030,15 +1035,25 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
         b->ntiles[j] = nt;
         d[j].tile0 = t0;
         d[j].ntiles = nt;
-        // dual strips of kBatchStripThreads / T pixels (T threads per pixel)
-        const int sp = lift::kBatchStripThreads >> (d[j].P.k >= 12 ? 2 : (d[j].P.k >= 6 ? 1 : 0));
-        d[j].strip0 = static_cast<int>(si.size());
-        d[j].nstrips = (d[j].P.N + sp - 1) / sp;
-        stage = std::max(stage, lift::batch_strip_stage(d[j].P.k));
+        // dual strips of the shape a single problem of this k takes
+        int sth = 0, sby = 0, spx = 0;
+        lift::strip_shape_of(d[j].P.k, &sth, &sby, &spx);
+        size_t g = 0;
+        while (g < gthreads.size() && gthreads[g] != sth) ++g;
+        if (g == gthreads.size()) {
+            gthreads.push_back(sth);
+            gstrips.emplace_back();
+            gbytes.push_back(0);
+        }
+        gbytes[g] = std::max(gbytes[g], sby);
+        d[j].strip0 = static_cast<int>(gstrips[g].size());
+        d[j].nstrips = (d[j].P.N + spx - 1) / spx;
+        gstrips[g].insert(gstrips[g].end(), d[j].nstrips, j);
         ti.insert(ti.end(), nt, j);
-        si.insert(si.end(), d[j].nstrips, j);
         t0 += nt;
     }
+    std::vector<int> si;
+    for (const auto &v : gstrips) si.insert(si.end(), v.begin(), v.end());
     const int ns = static_cast<int>(si.size());
     if (ti.empty()) ti.push_back(0);    // keep valid allocations; the totals stay 0
     if (si.empty()) si.push_back(0);
@@ -1048,6 +1063,17 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
     int rc = dev_alloc(reinterpret_cast<void **>(&b->tile_inst), ti.size() * sizeof(int));
     if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&b->strip_inst), si.size() * sizeof(int));
     if (rc != LIFT_OK) return rc;
+    b->groups.clear();
+    int off = 0;
+    for (size_t g = 0; g < gthreads.size(); ++g) {
+        lift::StripGroup G;
+        G.threads = gthreads[g];
+        G.bytes = gbytes[g];
+        G.nstrips = static_cast<int>(gstrips[g].size());
+        G.strip_inst = b->strip_inst + off;
+        off += G.nstrips;
+        b->groups.push_back(G);
+    }
     LIFT_CK(cudaMemcpyAsync(b->tile_inst, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b->stream));
     LIFT_CK(cudaMemcpyAsync(b->strip_inst, si.data(), si.size() * sizeof(int),
@@ -1057,7 +1083,6 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
     LIFT_CK(cudaStreamSynchronize(b->stream));   // host vectors die here
     b->total_tiles = t0;
     b->total_strips = ns;
-    b->strip_stage = stage;
     b->threads = threads;
     b->big_tiles = big_tiles;
     drop_graph(b);
@@ -1067,9 +1092,9 @@ int batch_set_tiles(lift_batch b, int threads, int big_tiles)
 int batch_launch(lift_batch b, int iters)
 {
     for (int it = 0; it < iters; ++it) {
-        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->strip_inst,
-                                             b->live, b->total_tiles, b->total_strips,
-                                             b->strip_stage, b->err, b->stream));
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->live,
+                                             b->total_tiles, b->groups.data(),
+                                             static_cast<int>(b->groups.size()), b->err, b->stream));
         for (size_t m = 0; m < b->big.size(); ++m) {
             const LiftState &S = b->S[b->big[m]];
             LIFT_CK(lift::launch_dual_step(b->Pbig[m], S, b->stream));
@@ -1080,7 +1105,7 @@ int batch_launch(lift_batch b, int iters)
 }
 
 // In a captured interval the merged launches stay on the batch stream and
-// the big instances, which share nothing, are spread over kBatchStreams
+// the big instances, which share nothing, are spread over nfork (at most kBatchStreams)
 // forked streams (all their iterations back to back), so that the dual steps
 // of one instance run beside the primal steps of another.
 int batch_launch_forked(lift_batch b, int iters)
@@ -1092,13 +1117,14 @@ int batch_launch_forked(lift_batch b, int iters)
         for (int j = 0; j <= kBatchStreams; ++j)
             LIFT_CK(cudaEventCreateWithFlags(&b->fork_e[j], cudaEventDisableTiming));
     }
-    const int ns = std::min(kBatchStreams, static_cast<int>(b->big.size()));
+    const int ns = std::min(std::max(1, std::min(b->nfork, kBatchStreams)),
+                            static_cast<int>(b->big.size()));
     LIFT_CK(cudaEventRecord(b->fork_e[kBatchStreams], b->stream));
     for (int j = 0; j < ns; ++j) LIFT_CK(cudaStreamWaitEvent(b->fork_s[j], b->fork_e[kBatchStreams], 0));
     for (int it = 0; it < iters; ++it)
-        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->strip_inst,
-                                             b->live, b->total_tiles, b->total_strips,
-                                             b->strip_stage, b->err, b->stream));
+        LIFT_CK(lift::launch_batch_iteration(b->threads, b->desc, b->tile_inst, b->live,
+                                             b->total_tiles, b->groups.data(),
+                                             static_cast<int>(b->groups.size()), b->err, b->stream));
     for (size_t m = 0; m < b->big.size(); ++m) {
         cudaStream_t st = b->fork_s[m % ns];
         const LiftState &S = b->S[b->big[m]];
@@ -1377,10 +1403,11 @@ int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen)
     if (!b || iters < 1) return LIFT_ERR_ARG;
     const int cand[3] = {128, 256, 512};
     // big-instance thresholds: none (all merged), 1, 2 and 4 full waves of
-    // 256-thread tiles
+    // 256-thread tiles; the big instances on 1, 2 or 4 streams at once
     const int thr[4] = {0, b->wave, 2 * b->wave, 4 * b->wave};
+    const int forks[3] = {1, 2, 4};
     float best_ms = 0.0f;
-    int best = lift::kStepThreads, best_big = b->big_tiles;
+    int best = lift::kStepThreads, best_big = b->big_tiles, best_fork = b->nfork;
     cudaEvent_t e0, e1;
     LIFT_CK(cudaEventCreate(&e0));
     LIFT_CK(cudaEventCreate(&e1));
@@ -1393,22 +1420,34 @@ int lift_batch_autotune(lift_batch b, int iters, int *threads_chosen)
             bool ok = true;
             for (int j = 0; j < b->n; ++j) ok = ok && (b->ntiles[j] == 0 || cand[c] >= b->P[j].k);
             if (!ok) continue;
-            rc = lift_batch_reset(b);
-            if (rc == LIFT_OK) rc = batch_launch(b, 2);           // warm-up
-            if (rc != LIFT_OK) break;
-            cudaEventRecord(e0, b->stream);
-            rc = batch_launch(b, iters);
-            cudaEventRecord(e1, b->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LIFT_ERR_CUDA; break; }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = cand[c]; best_big = thr[t]; }
+            for (int fk = 0; fk < 3 && rc == LIFT_OK; ++fk) {
+                if (forks[fk] > 1 && static_cast<int>(b->big.size()) < forks[fk]) continue;
+                b->nfork = forks[fk];
+                // time the captured interval that a solve would replay
+                rc = lift_batch_reset(b);
+                if (rc == LIFT_OK) rc = batch_capture(b, iters);
+                if (rc != LIFT_OK) break;
+                LIFT_CK(cudaGraphLaunch(b->exec, b->stream));           // warm-up
+                cudaEventRecord(e0, b->stream);
+                LIFT_CK(cudaGraphLaunch(b->exec, b->stream));
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LIFT_ERR_CUDA; break; }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (best_ms == 0.0f || ms < best_ms) {
+                    best_ms = ms;
+                    best = cand[c];
+                    best_big = thr[t];
+                    best_fork = forks[fk];
+                }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LIFT_OK) return rc;
-    rc = batch_set_tiles(b, best, best_big);
+    b->nfork = best_fork;
+    rc = batch_set_tiles(b, best, best_big);            // drops the last captured graph
     if (rc == LIFT_OK) rc = lift_batch_reset(b);
     if (rc == LIFT_OK && threads_chosen) *threads_chosen = best;
     return rc;
@@ -1427,6 +1466,17 @@ int lift_batch_set_schedule(lift_batch b, int threads, int big_tiles)
             rc = batch_set_tiles(b, old_threads, old_big);
             return rc != LIFT_OK ? rc : LIFT_ERR_ARG;
         }
+    return LIFT_OK;
+}
+
+int lift_batch_streams(lift_batch b, int set, int *n)
+{
+    if (!b || set < 0 || set > kBatchStreams) return LIFT_ERR_ARG;
+    if (set > 0 && set != b->nfork) {
+        b->nfork = set;
+        drop_graph(b);
+    }
+    if (n) *n = b->nfork;
     return LIFT_OK;
 }
 

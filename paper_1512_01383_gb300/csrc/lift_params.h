@@ -76,8 +76,6 @@ struct AdjState {
 };
 
 constexpr int kStepThreads = 256;
-// Threads of a CTA of the batched dual step (strips of 256 / T pixels).
-constexpr int kBatchStripThreads = 256;
 
 // pdhg_step.cu
 cudaError_t launch_dual_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
@@ -99,14 +97,24 @@ cudaError_t launch_dual_range(const LiftParams &P, const LiftState &S, int p0, i
 cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0, int p1,
                                 int origin, cudaStream_t st);
 
-// One iteration of the merged batch members: the dual step over all their
-// strips (strip_inst: instance of each strip; stage: shared bytes of the
-// largest strip stage, batch_strip_stage), the primal step over their tiles
-// of `threads` threads.  err: set non-zero if a bounded wait gave up.
+// The dual strips of the merged batch members with one CTA shape: threads
+// per CTA and dynamic shared bytes (the largest of the group's members),
+// and their instance list (device, nstrips entries).
+struct StripGroup {
+    int threads = 0, bytes = 0, nstrips = 0;
+    const int *strip_inst = nullptr;
+};
+
+// One iteration of the merged batch members: the dual step in one strip
+// launch per group (each member in the strips of a single problem of its
+// k), the primal step over their tiles of `threads` threads.  err: set
+// non-zero if a bounded wait gave up.
 cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *strip_inst, const int *live, int ntiles,
-                                   int nstrips, int stage, int *err, cudaStream_t st);
-int batch_strip_stage(int k);
+                                   const int *live, int ntiles, const StripGroup *groups,
+                                   int ngroups, int *err, cudaStream_t st);
+// The strip shape of a single problem with k intervals: threads per CTA and
+// dynamic shared bytes.
+void strip_shape_of(int k, int *threads, int *bytes, int *pixels);
 
 // adjoint.cu
 int adjoint_blocks(const LiftParams &P);

@@ -815,20 +815,20 @@ static cudaError_t launch_batch_primal(const InstDesc *D, const int *tile_inst, 
 }
 
 cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *tile_inst,
-                                   const int *strip_inst, const int *live, int ntiles,
-                                   int nstrips, int stage, int *err, cudaStream_t st)
+                                   const int *live, int ntiles, const StripGroup *groups,
+                                   int ngroups, int *err, cudaStream_t st)
 {
     if (ntiles <= 0) return cudaSuccess;
-    if (nstrips > 0) {
-        // every strip has kBatchStripThreads threads; stage: the largest staged records
-        const int bytes = stage + 64 * 16 + (kBatchStripThreads / 32) * 96 * 16;
-        if (bytes > kStripSmemCap) return cudaErrorInvalidValue;
+    for (int g = 0; g < ngroups; ++g) {
+        const StripGroup &G = groups[g];
+        if (G.nstrips <= 0) continue;
+        if (G.bytes > kStripSmemCap) return cudaErrorInvalidValue;
         int resident = 0;
-        cudaError_t e = strip_occupancy<0>(kBatchStripThreads, bytes, &resident);
+        cudaError_t e = strip_occupancy<0>(G.threads, G.bytes, &resident);
         if (e != cudaSuccess) return e;
         LiftParams none{};
-        dual_strip_kernel<0><<<nstrips, kBatchStripThreads, bytes, st>>>(none, nullptr, nullptr, nullptr,
-                                                                        0, 0, D, strip_inst, live, err, 0);
+        dual_strip_kernel<0><<<G.nstrips, G.threads, G.bytes, st>>>(none, nullptr, nullptr, nullptr,
+                                                                   0, 0, D, G.strip_inst, live, err, 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -840,10 +840,6 @@ cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *ti
     }
 }
 
-int batch_strip_stage(int k)
-{
-    return strip_smem(kBatchStripThreads >> strip_tshift(k), k, kBatchStripThreads).stage;
-}
 
 static inline int step_blocks(const LiftParams &P)
 {
@@ -861,6 +857,14 @@ static int strip_spp(int k)
     int spp = 256 >> ts;
     while (spp > step && strip_smem(spp, k, spp << ts).stage > kStripStage) spp -= step;
     return spp;
+}
+
+void strip_shape_of(int k, int *threads, int *bytes, int *pixels)
+{
+    const int spp = strip_spp(k);
+    *pixels = spp;
+    *threads = spp << strip_tshift(k);
+    *bytes = strip_smem(spp, k, *threads).bytes;
 }
 
 template <int KIND>

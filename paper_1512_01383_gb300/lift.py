@@ -34,7 +34,7 @@ EXPORTED = (
     "lift_set_params", "lift_unrolled_forward", "lift_unrolled_backward",
     "lift_get_balance", "lift_set_resident", "lift_set_bands", "lift_unrolled_generation",
     "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
-    "lift_cuda_error",
+    "lift_cuda_error", "lift_batch_streams",
 )
 
 
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         "lift_band_export": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "lift_band_import": (C.c_int, [vp, C.c_int, vp, C.c_int]),
         "lift_cuda_error": (C.c_char_p, []),
+        "lift_batch_streams": (C.c_int, [vp, C.c_int, ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -509,6 +510,13 @@ def lift_batch_autotune(b: int, iters: int) -> int:
 def lift_batch_set_schedule(b: int, threads: int, big_tiles: int) -> None:
     _check(load().lift_batch_set_schedule(C.c_void_p(b), threads, big_tiles),
            "lift_batch_set_schedule")
+
+
+def lift_batch_streams(b: int, set_to: int = 0) -> int:
+    """Set (1..4) and return the number of streams the big instances share."""
+    n = C.c_int()
+    _check(load().lift_batch_streams(C.c_void_p(b), set_to, C.byref(n)), "lift_batch_streams")
+    return n.value
 
 
 def lift_batch_schedule(b: int) -> tuple[int, int, int]:
