@@ -111,7 +111,9 @@ adj_primal_local_kernel(const LiftParams P, const float2 *__restrict__ x_n,
 
 // ---------------------------------------------------------------------------
 // Four blocks per SM (64 registers, a few bytes spilled): the dual-number
-// projection below otherwise holds 80 registers and leaves three.
+// projection below otherwise holds 80 registers and leaves three.  Records in
+// the epigraph of rho_i^* (the forward step's float test) take its identity
+// Jacobian; those below it are packed per warp into one dual-number pass.
 template <int KIND>
 __global__ void __launch_bounds__(kAdjThreads, 4)
 adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
@@ -123,6 +125,12 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
     __shared__ float2 s_a[kAdjThreads], s_b[kAdjThreads];
     __shared__ float2 s_la[kAdjThreads / 32], s_lb[kAdjThreads / 32];
     __shared__ double red[3][kAdjThreads / 32];
+    // per warp: the records below the graph of rho_i^*, packed for the
+    // dual-number projection, and its results for their owners
+    __shared__ float4 s_qa[kAdjThreads / 32][32];   // {y0, h0, a.x, a.y}
+    __shared__ float2 s_qb[kAdjThreads / 32][32];   // {f, gamma_i}
+    __shared__ float4 s_qr[kAdjThreads];            // {adj_v, adj_z, df, -} by owner
+    __shared__ unsigned char s_qo[kAdjThreads / 32][32];   // owner lane of each entry
     const int tid = threadIdx.x;
     int lp, i;
     split_thread_adj(P, tid, lp, i);
@@ -147,11 +155,14 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
 
     double gl = 0.0, ga = 0.0, gn = 0.0;
     float2 scan2_val = make_float2(0.0f, 0.0f);
-    float adj_v = 0.0f, adj_z = 0.0f, aq_tot = 0.0f;
+    float adj_v = 0.0f, adj_z = 0.0f, aq_tot = 0.0f, gfi = 0.0f;
     float2 adj_a = make_float2(0.0f, 0.0f);
+    float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float y0f = 0.0f, h0f = 0.0f, fpix = 0.0f;
+    bool below = false;
     if (active) {
         // --- complete the adjoint of y_{n+1}, q_{n+1} with the primal step's uses
-        float4 a = ay[o];
+        a = ay[o];
         const float gr = col + 1 < P.W ? G[o + P.k].x : 0.0f;
         const float gd = row + 1 < P.H ? G[o + static_cast<size_t>(P.W) * P.k].x : 0.0f;
         a.x += -P.tau_u * g.x + ic.y * ic.x * g.y - P.delta * (s1.total.x - s1.incl.x);
@@ -184,26 +195,58 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
         const float vh = d.x + ic.z * (xb.x + P.delta * tail - ic.x * xb.y);
         const float zh = d.y + ic.z * xb.y;
 
-        // --- epigraph projection: Jacobian w.r.t. (y0, h0, f, alpha, nu)
-        using D5 = Dual<5>;
-        const D5 y0 = D5::seed(vh * P.inv_delta, 0), h0 = D5::seed(zh * P.inv_delta, 1);
-        const D5 f = D5::seed(__ldg(P.f + pix), 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
-        const float l = ic.x, r = ic.x + P.delta;
-        QPieceT<D5> qp;
-        if (P.kind == 3)
-            qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
-        else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
-        else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
-        D5 yo, ho;
-        qpiece_project(qp, y0, h0, yo, ho);
-        // (v', z') = Delta (yo, ho)((v^, z^)/Delta)
-        adj_v = a.x * yo.d[0] + a.y * ho.d[0];
-        adj_z = a.x * yo.d[1] + a.y * ho.d[1];
-        const float gfi = P.delta * (a.x * yo.d[2] + a.y * ho.d[2]);
-        ga += static_cast<double>(P.delta * (a.x * yo.d[3] + a.y * ho.d[3]));
-        gn += static_cast<double>(P.delta * (a.x * yo.d[4] + a.y * ho.d[4]));
-        scan2_val = make_float2(ic.z * adj_v, gfi);
+        // --- epigraph projection: in the epigraph it is the identity (the
+        // forward step's test, in float); below it, its Jacobian with respect
+        // to (y0, h0, f, alpha, nu) comes from the packed pass below
+        y0f = vh * P.inv_delta;
+        h0f = zh * P.inv_delta;
+        fpix = __ldg(P.f + pix);
+        below = !(h0f >= quad_conj_direct(P, fpix, ic.x, ic.x + P.delta, y0f));
+        adj_v = a.x;
+        adj_z = a.y;
     }
+    {
+        // the warp's records below the graph, one per lane of one pass
+        const int lane = tid & 31, wq = tid >> 5;
+        const unsigned m = __ballot_sync(0xffffffffu, below);
+        const int slot = __popc(m & ((1u << lane) - 1u)), nq = __popc(m);
+        if (below) {
+            s_qa[wq][slot] = make_float4(y0f, h0f, a.x, a.y);
+            s_qb[wq][slot] = make_float2(fpix, ic.x);
+            s_qo[wq][slot] = static_cast<unsigned char>(lane);
+        }
+        __syncwarp();
+        if (lane < nq) {
+            const float4 e = s_qa[wq][lane];
+            const float2 eb = s_qb[wq][lane];
+            using D5 = Dual<5>;
+            const D5 y0 = D5::seed(e.x, 0), h0 = D5::seed(e.y, 1);
+            const D5 f = D5::seed(eb.x, 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
+            const float l = eb.y, r = eb.y + P.delta;
+            QPieceT<D5> qp;
+            if (P.kind == 3)
+                qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
+            else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
+            else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
+            D5 yo, ho;
+            qpiece_project(qp, y0, h0, yo, ho);
+            // (v', z') = Delta (yo, ho)((v^, z^)/Delta)
+            const float av = e.z * yo.d[0] + e.w * ho.d[0];
+            const float az = e.z * yo.d[1] + e.w * ho.d[1];
+            const float df = P.delta * (e.z * yo.d[2] + e.w * ho.d[2]);
+            ga += static_cast<double>(P.delta * (e.z * yo.d[3] + e.w * ho.d[3]));
+            gn += static_cast<double>(P.delta * (e.z * yo.d[4] + e.w * ho.d[4]));
+            s_qr[(wq << 5) + s_qo[wq][lane]] = make_float4(av, az, df, 0.0f);   // to its owner
+        }
+        __syncwarp();
+        if (below) {
+            const float4 rr = s_qr[tid];
+            adj_v = rr.x;
+            adj_z = rr.y;
+            gfi = rr.z;
+        }
+    }
+    if (active) scan2_val = make_float2(ic.z * adj_v, gfi);
     // scan 2: {sigma adj_v^} (pulled back through the tail sums) and f's
     // gradient summed over the pixel's intervals
     const Scan2 s2 = seg_scan2(scan2_val, lp * P.k, P.k, tid, active, s_b, s_lb);
