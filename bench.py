@@ -56,8 +56,8 @@ PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel sources
 # whose SHA-256 (of the files below, in this order) is DUAL_TRAFFIC_SRC; with
 # any other source the bench reports no traffic figure.
-DUAL_TRAFFIC_NCU = None
-DUAL_TRAFFIC_SRC = None
+DUAL_TRAFFIC_NCU = 149923328          # 121 714 688 read + 28 208 640 written
+DUAL_TRAFFIC_SRC = "27af94b52f122c6223bbc2ded9b171612036b33620be062bba95339a7308eb12"
 DUAL_KERNEL_FILES = ("pdhg_step.cu", "lift_device.cuh", "lift_bulk.cuh", "lift_params.h",
                      "lift_tile.cuh")
 
