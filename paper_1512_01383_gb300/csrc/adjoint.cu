@@ -8,15 +8,23 @@
 // evaluated on forward-mode dual numbers (lift_ad.cuh).
 //
 // With x = (u, s), xbar, y = (v, z, px, py), q and adjoints ax, axb, ay, aq,
-// one reverse iteration is three kernels:
-//   adj_primal_local : g_u = [0 < w < 1](ax.u + 2 axb.u), g_s = ax.s + 2 axb.s
+// one reverse iteration is two kernels:
+//   adj_primal_local : completes axb.u with the neighbours' part of grad^T
+//                      left by the previous reverse iteration (A), then
+//                      g_u = [0 < w < 1](ax.u + 2 axb.u), g_s = ax.s + 2 axb.s
 //                      (w = the unclamped primal update), ax <- g - axb
-//   adj_dual_local   : completes ay, aq with the primal step's uses of y, q,
+//   adj_dual_strip   : completes ay, aq with the primal step's uses of y, q,
 //                      then pulls them back through the dual step: the ball
 //                      and epigraph projections, the ascent and the sums over
-//                      intervals; writes ay, aq, the own part of axb, f's
-//                      gradient and per-block sums of the scalar gradients
-//   adj_dual_gather  : adds the neighbours' part of grad^T to axb.u
+//                      intervals; writes ay, aq, the own part of axb, the
+//                      neighbours' part (A), f's gradient and per-CTA sums of
+//                      the scalar gradients
+// adj_dual_strip runs on strips of pixels like the forward dual step: T
+// threads share a pixel, each owning consecutive intervals, so the sums over
+// a pixel's intervals are running sums; the records below the graph of
+// rho_i^* are pooled over the CTA and their Jacobians computed on full warps.
+// Above 8 intervals per thread (k > 32) the record-per-thread form
+// (adj_dual_local, then adj_dual_gather) runs instead.
 #include "lift_ad.cuh"
 #include "lift_device.cuh"
 #include "lift_params.h"
@@ -84,13 +92,47 @@ __device__ __forceinline__ float div_p(const LiftParams &P, const float4 *__rest
     return dv;
 }
 
+// The epigraph projection of a record below the graph of rho_i^*, pulled
+// back: (y0, h0) = (v^, z^)/Delta, the adjoint (ax, ay) of the projected
+// (v', z') = Delta (yo, ho), the pixel's f and the interval's left label l.
+// Returns the adjoint of (v^, z^) in (av, az), and Delta times the adjoint's
+// derivative with respect to f, alpha and nu in df, dga, dgn: the piece and
+// projection code of the forward step evaluated on dual numbers seeded in
+// (y0, h0, f, alpha, nu).
+__device__ __forceinline__ void epi_pullback(const LiftParams &P, float y0v, float h0v, float ax,
+                                             float ay, float fv, float l, float &av, float &az,
+                                             float &df, float &dga, float &dgn)
+{
+    using D5 = Dual<5>;
+    const D5 y0 = D5::seed(y0v, 0), h0 = D5::seed(h0v, 1);
+    const D5 f = D5::seed(fv, 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
+    const float r = l + P.delta;
+    QPieceT<D5> qp;
+    if (P.kind == 3)
+        qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
+    else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
+    else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
+    D5 yo, ho;
+    qpiece_project(qp, y0, h0, yo, ho);
+    // (v', z') = Delta (yo, ho)((v^, z^)/Delta)
+    av = ax * yo.d[0] + ay * ho.d[0];
+    az = ax * yo.d[1] + ay * ho.d[1];
+    df = P.delta * (ax * yo.d[2] + ay * ho.d[2]);
+    dga = P.delta * (ax * yo.d[3] + ay * ho.d[3]);
+    dgn = P.delta * (ax * yo.d[4] + ay * ho.d[4]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// A (may be null): the neighbours' part of grad^T from the previous reverse
+// iteration's dual kernel, added to axb.u here (the same sum, in the same
+// order, as adj_dual_gather).
 __global__ void __launch_bounds__(kAdjThreads)
 adj_primal_local_kernel(const LiftParams P, const float2 *__restrict__ x_n,
                         const float4 *__restrict__ y_n1, float2 *__restrict__ ax,
-                        const float2 *__restrict__ axb, float2 *__restrict__ G)
+                        const float2 *__restrict__ axb, float2 *__restrict__ G,
+                        const float2 *__restrict__ A)
 {
     int lp, i;
     split_thread_adj(P, threadIdx.x, lp, i);
@@ -102,7 +144,14 @@ adj_primal_local_kernel(const LiftParams P, const float2 *__restrict__ x_n,
     const float4 d = y_n1[o];
     const float dv = div_p(P, y_n1, o, row, col, d);
     const float w = xo.x - P.tau_u * (d.x - dv);
-    const float2 a = ax[o], b = axb[o];
+    const float2 a = ax[o];
+    float2 b = axb[o];
+    if (A) {
+        float add = 0.0f;
+        if (col > 0) add += P.sigma_p * A[o - P.k].x;
+        if (row > 0) add += P.sigma_p * A[o - static_cast<size_t>(P.W) * P.k].y;
+        b.x += add;
+    }
     const float gu = (w > 0.0f && w < 1.0f) ? a.x + 2.0f * b.x : 0.0f;
     const float gs = a.y + 2.0f * b.y;
     G[o] = make_float2(gu, gs);
@@ -219,23 +268,10 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
         if (lane < nq) {
             const float4 e = s_qa[wq][lane];
             const float2 eb = s_qb[wq][lane];
-            using D5 = Dual<5>;
-            const D5 y0 = D5::seed(e.x, 0), h0 = D5::seed(e.y, 1);
-            const D5 f = D5::seed(eb.x, 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
-            const float l = eb.y, r = eb.y + P.delta;
-            QPieceT<D5> qp;
-            if (P.kind == 3)
-                qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
-            else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
-            else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
-            D5 yo, ho;
-            qpiece_project(qp, y0, h0, yo, ho);
-            // (v', z') = Delta (yo, ho)((v^, z^)/Delta)
-            const float av = e.z * yo.d[0] + e.w * ho.d[0];
-            const float az = e.z * yo.d[1] + e.w * ho.d[1];
-            const float df = P.delta * (e.z * yo.d[2] + e.w * ho.d[2]);
-            ga += static_cast<double>(P.delta * (e.z * yo.d[3] + e.w * ho.d[3]));
-            gn += static_cast<double>(P.delta * (e.z * yo.d[4] + e.w * ho.d[4]));
+            float av, az, df, dga, dgn;
+            epi_pullback(P, e.x, e.y, e.z, e.w, eb.x, eb.y, av, az, df, dga, dgn);
+            ga += static_cast<double>(dga);
+            gn += static_cast<double>(dgn);
             s_qr[(wq << 5) + s_qo[wq][lane]] = make_float4(av, az, df, 0.0f);   // to its owner
         }
         __syncwarp();
@@ -302,6 +338,211 @@ adj_dual_gather_kernel(const LiftParams P, const float2 *__restrict__ A, float2 
     axb[o].x += add;
 }
 
+// ---------------------------------------------------------------------------
+// The reverse dual step on strips of `spp` consecutive pixels, one strip per
+// CTA, 2^ts threads per pixel; thread j of a pixel owns the intervals
+// [j c, min((j+1) c, k)), c = ceil(k / 2^ts) <= C.  Shared memory: one queue
+// slot per record of the strip ({y0, h0, a_v, a_z} and {f, gamma_i}), filled
+// with the records below the graph of rho_i^*; after one barrier the CTA's
+// threads take the queue in passes of one entry per thread, each entry's
+// results written back into its slot for the owner.
+constexpr int kAdjMaxChunk = 8;
+constexpr int kAdjStripRecords = 1024;
+
+template <int C>
+__global__ void __launch_bounds__(256, 4)
+adj_dual_strip_kernel(const LiftParams P, int spp, int ts, const float2 *__restrict__ xbar_n,
+                      const float4 *__restrict__ y_n, const float2 *__restrict__ G,
+                      float4 *__restrict__ ay, float *__restrict__ aq, float2 *__restrict__ axb,
+                      float2 *__restrict__ A, float *__restrict__ gf, double *__restrict__ partial)
+{
+    extern __shared__ float4 adj_smem[];
+    __shared__ int s_n;
+    __shared__ double red[3][8];
+    const int nrec = spp * P.k;
+    float4 *s_qa = adj_smem;                                        // [nrec]
+    float2 *s_qb = reinterpret_cast<float2 *>(adj_smem + nrec);     // [nrec]
+    const int tid = threadIdx.x, T = 1 << ts, k = P.k;
+    const int lp = tid >> ts, j = tid & (T - 1);
+    const int c = (k + T - 1) >> ts;
+    const int pix = blockIdx.x * spp + lp;
+    const bool active = lp < spp && pix < P.N;
+    const int lo = j * c, hi = min(lo + c, k);
+    const size_t ob = static_cast<size_t>(active ? pix : 0) * k;
+    int row = 0, col = 0;
+    float aq_in = 0.0f, fpix = 0.0f;
+    if (active) {
+        row = pixel_row_adj(P, pix);
+        col = pix - row * P.W;
+        aq_in = aq[pix];                        // read before any write of this kernel
+        fpix = __ldg(P.f + pix);
+    }
+    if (tid == 0) s_n = 0;
+
+    // own sums of tau_s g_s and sbar over this thread's intervals
+    float2 g[C], xb[C];
+    float own_g = 0.0f, own_s = 0.0f;
+#pragma unroll
+    for (int it = 0; it < C; ++it) {
+        const int i = lo + it;
+        const bool ok = active && i < hi;
+        g[it] = ok ? G[ob + i] : make_float2(0.0f, 0.0f);
+        xb[it] = ok ? xbar_n[ob + i] : make_float2(0.0f, 0.0f);
+        if (ok) {
+            own_g += __ldg(P.icst + i).y * g[it].y;
+            own_s += xb[it].y;
+        }
+    }
+    // the later threads' sums of this pixel, and the pixel's total of tau_s g_s
+    float later_g = 0.0f, later_s = 0.0f;
+    for (int d = 1; d < T; ++d) {
+        const float a = __shfl_down_sync(0xffffffffu, own_g, d, T);
+        const float b = __shfl_down_sync(0xffffffffu, own_s, d, T);
+        if (j + d < T) { later_g += a; later_s += b; }
+    }
+    const float total_g = __shfl_sync(0xffffffffu, own_g + later_g, 0, T);
+    const float aq_tot = aq_in + P.delta * total_g;
+    __syncthreads();                            // s_n initialised
+
+    // per record, from the last interval to the first: complete the adjoint
+    // of y with the primal step's uses, recompute the dual step's values,
+    // pull back through the ball projection; queue the records below the graph
+    float av[C], az[C];
+    float2 aa[C];
+    int slot[C];
+    double gl = 0.0, ga = 0.0, gn = 0.0;
+    float run_g = later_g, run_s = later_s;
+#pragma unroll
+    for (int it = C - 1; it >= 0; --it) {
+        const int i = lo + it;
+        const bool ok = active && i < hi;
+        av[it] = 0.0f; az[it] = 0.0f; aa[it] = make_float2(0.0f, 0.0f); slot[it] = -1;
+        if (!ok) continue;
+        const size_t o = ob + i;
+        const float4 ic = __ldg(P.icst + i);    // {gamma_i, tau_s, sigma_vz, lambda Delta}
+        const float after_g = run_g, after_s = run_s;   // sums over l > i
+        run_g += ic.y * g[it].y;
+        run_s += xb[it].y;
+        float4 a = ay[o];
+        const float gr = col + 1 < P.W ? G[o + k].x : 0.0f;
+        const float gd = row + 1 < P.H ? G[o + static_cast<size_t>(P.W) * k].x : 0.0f;
+        a.x += -P.tau_u * g[it].x + ic.y * ic.x * g[it].y - P.delta * after_g;
+        a.y += -ic.y * g[it].y;
+        if (col + 1 < P.W) a.z += P.tau_u * (g[it].x - gr);
+        if (row + 1 < P.H) a.w += P.tau_u * (g[it].x - gd);
+        const float4 d = y_n[o];
+        const float gx = col + 1 < P.W ? xbar_n[o + k].x - xb[it].x : 0.0f;
+        const float gy = row + 1 < P.H ? xbar_n[o + static_cast<size_t>(P.W) * k].x - xb[it].x : 0.0f;
+        const float px = d.z + P.sigma_p * gx;
+        const float py = d.w + P.sigma_p * gy;
+        float2 adj_a = make_float2(a.z, a.w);
+        if (P.aniso) {
+            // componentwise clamp to [-R, R]: identity inside, the bound outside
+            if (fabsf(px) > ic.w) { gl += static_cast<double>(P.delta * copysignf(1.0f, px) * a.z); adj_a.x = 0.0f; }
+            if (fabsf(py) > ic.w) { gl += static_cast<double>(P.delta * copysignf(1.0f, py) * a.w); adj_a.y = 0.0f; }
+        } else {
+            const float n2 = px * px + py * py;
+            if (n2 > ic.w * ic.w) {
+                // p' = R a/|a|: J = (R/|a|)(I - a a^T/|a|^2), dp'/dR = a/|a|, R = lambda Delta
+                const float inv = rsqrtf(n2);
+                const float hx = px * inv, hy = py * inv;
+                const float dot = hx * a.z + hy * a.w;
+                adj_a = make_float2(ic.w * inv * (a.z - hx * dot), ic.w * inv * (a.w - hy * dot));
+                gl += static_cast<double>(P.delta * dot);
+            }
+        }
+        aa[it] = adj_a;
+        const float vh = d.x + ic.z * (xb[it].x + P.delta * after_s - ic.x * xb[it].y);
+        const float zh = d.y + ic.z * xb[it].y;
+        const float y0f = vh * P.inv_delta, h0f = zh * P.inv_delta;
+        av[it] = a.x;
+        az[it] = a.y;
+        // in the epigraph (the forward step's test, in float) the projection
+        // is the identity; below it the pooled pass computes its Jacobian
+        if (!(h0f >= quad_conj_direct(P, fpix, ic.x, ic.x + P.delta, y0f))) {
+            const int e = atomicAdd(&s_n, 1);
+            s_qa[e] = make_float4(y0f, h0f, a.x, a.y);
+            s_qb[e] = make_float2(fpix, ic.x);
+            slot[it] = e;
+        }
+    }
+    __syncthreads();
+    const int nq = s_n;
+    for (int e = tid; e < nq; e += blockDim.x) {
+        const float4 q = s_qa[e];
+        const float2 qb = s_qb[e];
+        float rv, rz, df, dga, dgn;
+        epi_pullback(P, q.x, q.y, q.z, q.w, qb.x, qb.y, rv, rz, df, dga, dgn);
+        s_qa[e] = make_float4(rv, rz, df, dga);
+        s_qb[e] = make_float2(dgn, 0.0f);
+    }
+    __syncthreads();
+
+    // the pulled-back records, f's gradient, and the prefix sums over l < i of
+    // sigma_l adj_v_l for the ascent of s
+    float gfi = 0.0f, own_v = 0.0f;
+#pragma unroll
+    for (int it = 0; it < C; ++it) {
+        const int i = lo + it;
+        if (!(active && i < hi)) continue;
+        if (slot[it] >= 0) {
+            const float4 r = s_qa[slot[it]];
+            av[it] = r.x;
+            az[it] = r.y;
+            gfi += r.z;
+            ga += static_cast<double>(r.w);
+            gn += static_cast<double>(s_qb[slot[it]].x);
+        }
+        own_v += __ldg(P.icst + i).z * av[it];
+    }
+    float before_v = 0.0f, tot_f = gfi;
+    for (int d = 1; d < T; ++d) {
+        const float a = __shfl_up_sync(0xffffffffu, own_v, d, T);
+        if (j >= d) before_v += a;
+    }
+    for (int d = 1; d < T; d <<= 1) tot_f += __shfl_xor_sync(0xffffffffu, tot_f, d, T);
+    float run_v = before_v;
+#pragma unroll
+    for (int it = 0; it < C; ++it) {
+        const int i = lo + it;
+        if (!(active && i < hi)) continue;
+        const size_t o = ob + i;
+        const float4 ic = __ldg(P.icst + i);
+        const float head = run_v;               // sum over l < i of sigma_l adj_v_l
+        run_v += ic.z * av[it];
+        ay[o] = make_float4(av[it], az[it], aa[it].x, aa[it].y);
+        A[o] = aa[it];
+        // own part of grad^T (the neighbours' part is added by the next
+        // reverse iteration's primal kernel)
+        float au = ic.z * av[it];
+        if (col + 1 < P.W) au -= P.sigma_p * aa[it].x;
+        if (row + 1 < P.H) au -= P.sigma_p * aa[it].y;
+        const float as = -ic.z * ic.x * av[it] + ic.z * az[it] + P.delta * head -
+                         P.sigma_q * P.delta * aq_tot;
+        axb[o] = make_float2(au, as);
+    }
+    if (active && j == 0) {
+        aq[pix] = aq_tot;
+        gf[pix] += tot_f;
+    }
+    // per-CTA sums of the scalar gradients (fixed order) into the CTA's slot
+    for (int off = 16; off > 0; off >>= 1) {
+        gl += __shfl_down_sync(0xffffffffu, gl, off);
+        ga += __shfl_down_sync(0xffffffffu, ga, off);
+        gn += __shfl_down_sync(0xffffffffu, gn, off);
+    }
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) { red[0][wid] = gl; red[1][wid] = ga; red[2][wid] = gn; }
+    __syncthreads();
+    if (tid == 0) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) { a0 += red[0][w]; a1 += red[1][w]; a2 += red[2][w]; }
+        partial[3 * blockIdx.x + 0] += a0;
+        partial[3 * blockIdx.x + 1] += a1;
+        partial[3 * blockIdx.x + 2] += a2;
+    }
+}
+
 // Sum the per-block scalar partials into acc[3] in a fixed order.
 __global__ void adj_finish_kernel(const double *__restrict__ partial, int nblocks,
                                   double *__restrict__ acc)
@@ -337,8 +578,30 @@ __global__ void adj_seed_kernel(const LiftParams P, const float *__restrict__ gr
 }
 
 // ---------------------------------------------------------------------------
+// Strip geometry of the reverse dual step: 2^ts threads per pixel (as the
+// forward strips), c = ceil(k / 2^ts) intervals per thread, at most
+// kAdjMaxChunk (else the record-per-thread kernels run: returns false);
+// 128 / 2^ts pixels per strip (128 threads: smaller CTAs wait less on one
+// another at the barriers around the pooled pass; 56.8 against 58.4 ms for
+// the 500-iteration reverse pass at 256^2, L = 16), fewer (in steps of a
+// warp's pixels) while the strip holds more than kAdjStripRecords records.
+static bool adj_strip_shape(const LiftParams &P, int *spp, int *ts, int *c)
+{
+    const int t = P.k >= 12 ? 2 : (P.k >= 6 ? 1 : 0);
+    const int cc = (P.k + (1 << t) - 1) >> t;
+    if (cc > kAdjMaxChunk || P.D > 1) return false;
+    int n = 128 >> t;
+    while (n > (32 >> t) && n * P.k > kAdjStripRecords) n -= 32 >> t;
+    *spp = n;
+    *ts = t;
+    *c = cc;
+    return true;
+}
+
 int adjoint_blocks(const LiftParams &P)
 {
+    int spp, ts, c;
+    if (adj_strip_shape(P, &spp, &ts, &c)) return (P.N + spp - 1) / spp;
     return (P.N + P.ppb - 1) / P.ppb;
 }
 
@@ -349,13 +612,47 @@ cudaError_t launch_adj_seed(const LiftParams &P, const float *grad_u, float2 *ax
     return cudaGetLastError();
 }
 
+template <int C>
+static cudaError_t launch_adj_strips(const LiftParams &P, int spp, int ts, const LiftState &Sn,
+                                     const AdjState &Aj, cudaStream_t st)
+{
+    const int nb = (P.N + spp - 1) / spp;
+    const size_t bytes = static_cast<size_t>(spp) * P.k * (sizeof(float4) + sizeof(float2));
+    if (bytes > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(adj_dual_strip_kernel<C>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(bytes));
+        if (e != cudaSuccess) return e;
+    }
+    adj_dual_strip_kernel<C><<<nb, spp << ts, bytes, st>>>(P, spp, ts, Sn.xbar, Sn.y, Aj.G, Aj.ay,
+                                                           Aj.aq, Aj.axb, Aj.A, Aj.gf, Aj.partial);
+    return cudaGetLastError();
+}
+
+// Aj.A must hold zeros before the first reverse iteration (the primal kernel
+// adds the previous iteration's neighbour terms from it).
 cudaError_t launch_adj_iteration(const LiftParams &P, const LiftState &Sn, const LiftState &Sn1,
                                  const AdjState &Aj, cudaStream_t st)
 {
-    const int nb = adjoint_blocks(P);
-    adj_primal_local_kernel<<<nb, kAdjThreads, 0, st>>>(P, Sn.x, Sn1.y, Aj.ax, Aj.axb, Aj.G);
+    const int nb = (P.N + P.ppb - 1) / P.ppb;
+    int spp, ts, c;
+    const bool strips = adj_strip_shape(P, &spp, &ts, &c);
+    adj_primal_local_kernel<<<nb, kAdjThreads, 0, st>>>(P, Sn.x, Sn1.y, Aj.ax, Aj.axb, Aj.G,
+                                                        strips ? Aj.A : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (strips) {
+        switch (c) {
+        case 1: return launch_adj_strips<1>(P, spp, ts, Sn, Aj, st);
+        case 2: return launch_adj_strips<2>(P, spp, ts, Sn, Aj, st);
+        case 3: return launch_adj_strips<3>(P, spp, ts, Sn, Aj, st);
+        case 4: return launch_adj_strips<4>(P, spp, ts, Sn, Aj, st);
+        case 5: return launch_adj_strips<5>(P, spp, ts, Sn, Aj, st);
+        case 6: return launch_adj_strips<6>(P, spp, ts, Sn, Aj, st);
+        case 7: return launch_adj_strips<7>(P, spp, ts, Sn, Aj, st);
+        default: return launch_adj_strips<8>(P, spp, ts, Sn, Aj, st);
+        }
+    }
     adj_dual_local_kernel<0><<<nb, kAdjThreads, 0, st>>>(P, Sn.xbar, Sn.y, Aj.G, Aj.ay, Aj.aq,
                                                          Aj.axb, Aj.A, Aj.gf, Aj.partial);
     e = cudaGetLastError();

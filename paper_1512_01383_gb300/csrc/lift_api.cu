@@ -1644,6 +1644,7 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f, do
     LIFT_CK(cudaMemsetAsync(A.ay, 0, Nk * sizeof(float4), h->stream));
     LIFT_CK(cudaMemsetAsync(A.aq, 0, N * sizeof(float), h->stream));
     LIFT_CK(cudaMemsetAsync(A.gf, 0, N * sizeof(float), h->stream));
+    LIFT_CK(cudaMemsetAsync(A.A, 0, Nk * sizeof(float2), h->stream));
     LIFT_CK(cudaMemsetAsync(A.acc, 0, 3 * sizeof(double), h->stream));
     LIFT_CK(cudaMemsetAsync(A.partial, 0, 3 * sizeof(double) * lift::adjoint_blocks(h->P),
                             h->stream));
