@@ -655,16 +655,31 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
 // after the scan).
 // The pixels [p0, p1); block b takes the tiles starting at tbase + 2b ppb
 // and tbase + (2b + 1) ppb (tbase <= p0; pixels before p0 are idle).
+// ahead > 0 (images): thread 0 also prefetches into L2 the records of block
+// blockIdx.x + ahead, the block that takes this one's place on the SM.
 template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
 primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q,
-                   const float *__restrict__ pz, int tbase, int p0, int p1)
+                   const float *__restrict__ pz, int tbase, int p0, int p1, int ahead)
 {
     __shared__ float2 s_in[kStepThreads];
     __shared__ float2 s_last[kStepThreads / 32];
     if (LIVE && *P.live == 0) return;
     const int tid = threadIdx.x;
+    if (!VOL && ahead > 0 && tid == 0) {
+        const long long b0 = tbase + 2LL * (blockIdx.x + ahead) * P.ppb;
+        const long long a = b0 > p0 ? b0 : p0;
+        const long long e = b0 + 2LL * P.ppb < p1 ? b0 + 2LL * P.ppb : p1;
+        if (a < e) {
+            bulk_prefetch_l2(y + a * P.k, static_cast<uint32_t>((e - a) * P.k * 16));
+            // the x records' 16-byte aligned part
+            const uintptr_t xa = (reinterpret_cast<uintptr_t>(x + a * P.k) + 15) & ~uintptr_t(15);
+            const uintptr_t xe = reinterpret_cast<uintptr_t>(x + e * P.k) & ~uintptr_t(15);
+            if (xe > xa)
+                bulk_prefetch_l2(reinterpret_cast<const void *>(xa), static_cast<uint32_t>(xe - xa));
+        }
+    }
     int lp, i;
     split_thread(P, tid, lp, i);
     int pix[2]; bool act[2]; size_t o[2]; float4 d[2]; float2 xo[2];
@@ -918,6 +933,30 @@ cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, in
 }
 
 // Primal half-step on the tiles [t0, t1) (two tiles per block).
+// Blocks of the image primal kernel resident on the current device at once
+// (the same for LIVE true and false), looked up once per device.
+static cudaError_t primal_resident(int *ctas)
+{
+    static std::mutex mu;
+    static int known[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) { *ctas = 0; return cudaSuccess; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (known[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, primal_step_kernel<false, false>,
+                                                          kStepThreads, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        known[dev] = per_sm * sms > 0 ? per_sm * sms : -1;
+    }
+    *ctas = known[dev] > 0 ? known[dev] : 0;
+    return cudaSuccess;
+}
+
 cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                                cudaStream_t st)
 {
@@ -933,15 +972,20 @@ cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0,
     const int r = ((p0 - origin) % P.ppb + P.ppb) % P.ppb;
     const int tbase = p0 - r;
     const int nb = (p1 - tbase + 2 * P.ppb - 1) / (2 * P.ppb);
-    if (P.D > 1)
+    if (P.D > 1) {
         primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz,
-                                                                     tbase, p0, p1);
-    else if (P.live != nullptr)
+                                                                     tbase, p0, p1, 0);
+        return cudaGetLastError();
+    }
+    int ahead = 0;
+    const cudaError_t e = primal_resident(&ahead);
+    if (e != cudaSuccess) return e;
+    if (P.live != nullptr)
         primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
-                                                                     tbase, p0, p1);
+                                                                     tbase, p0, p1, ahead);
     else
         primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
-                                                                      tbase, p0, p1);
+                                                                      tbase, p0, p1, ahead);
     return cudaGetLastError();
 }
 
