@@ -1651,16 +1651,16 @@ int lift_unrolled_backward(lift_handle h, const float *grad_u, float *grad_f, do
     const int nck = (h->unrolled_iters + C - 1) / C;
     for (int c = nck - 1; c >= 0; --c) {
         const int len = std::min(C, h->unrolled_iters - c * C);
-        // recompute the segment's states from its checkpoint
-        int rc = copy_state_dev(h, state_at(h, h->seg), state_at(h, h->ckpt + sb * c));
-        for (int j = 0; j < len && rc == LIFT_OK; ++j) {
-            rc = copy_state_dev(h, state_at(h, h->seg + sb * (j + 1)), state_at(h, h->seg + sb * j));
-            if (rc == LIFT_OK) rc = iterate_state(h, state_at(h, h->seg + sb * (j + 1)), 1);
-        }
-        if (rc != LIFT_OK) return rc;
+        // recompute the segment's states from its checkpoint: state 0 is the
+        // checkpoint itself, state j + 1 is written by one iteration from
+        // state j (no copy; the checkpoint is only read)
+        auto seg_state = [&](int j) {
+            return state_at(h, j == 0 ? h->ckpt + sb * c : h->seg + sb * j);
+        };
+        for (int j = 0; j < len; ++j)
+            LIFT_CK(lift::launch_iteration_into(h->P, seg_state(j), seg_state(j + 1), h->stream));
         for (int j = len - 1; j >= 0; --j)
-            LIFT_CK(lift::launch_adj_iteration(h->P, state_at(h, h->seg + sb * j),
-                                               state_at(h, h->seg + sb * (j + 1)), A, h->stream));
+            LIFT_CK(lift::launch_adj_iteration(h->P, seg_state(j), seg_state(j + 1), A, h->stream));
     }
     LIFT_CK(lift::launch_adj_finish(h->P, A, h->stream));
     if (grad_f)

@@ -86,6 +86,10 @@ cudaError_t launch_dual_band(const LiftParams &P, const LiftState &S, int t0, in
 cudaError_t launch_primal_band(const LiftParams &P, const LiftState &S, int t0, int t1,
                                cudaStream_t st);
 cudaError_t launch_primal_step(const LiftParams &P, const LiftState &S, cudaStream_t st);
+// One whole iteration from Sin into Sout (images, quadratic kinds; Sin is not
+// modified): bitwise the in-place iteration of Sin.
+cudaError_t launch_iteration_into(const LiftParams &P, const LiftState &Sin, const LiftState &Sout,
+                                  cudaStream_t st);
 // The half-steps on the pixels [p0, p1) of an image.  Tiles (the primal
 // step's, and the dual step's of sampled costs) start on the pixels
 // congruent to `origin` modulo the tile length, so the

@@ -254,8 +254,8 @@ __host__ __device__ inline int strip_tshift(int k)
 // float2 of slack in front for a first record that sits 8 bytes past a
 // 16-byte boundary, one behind), then xbar of the row below (same slack), then
 // the per-interval constants (k float4), one 64-entry projection ring per
-// warp and the CTA's pool of left-over entries (32 per warp).  `stage` (the
-// three record arrays) is rounded to 128 bytes.
+// warp and the CTA's pool of left-over entries (32 per warp), each entry 8
+// bytes.  `stage` (the three record arrays) is rounded to 128 bytes.
 struct StripSmem {
     int x_off, d_off, stage, ic_off, ring_off, pool_off, bytes;
 };
@@ -272,8 +272,8 @@ __host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
     L.stage = (o + 127) & ~127;
     L.ic_off = L.stage;
     L.ring_off = L.ic_off + k * 16;
-    L.pool_off = L.ring_off + (threads / 32) * 64 * 16;
-    L.bytes = L.pool_off + (threads / 32) * 32 * 16;
+    L.pool_off = L.ring_off + (threads / 32) * 64 * 8;
+    L.bytes = L.pool_off + (threads / 32) * 32 * 8;
     return L;
 }
 
@@ -310,18 +310,18 @@ __device__ __forceinline__ void x_ragged(const XRange &R, const float2 *__restri
 }
 
 // Projection of one queued record onto Delta * epi(rho_i^*), written back into
-// the staged y.  e = {record index in the strip, pixel, f of the pixel (the
-// quadratic kinds)}; the record holds the unscaled point (y0, h0) = (v, z) /
-// Delta until then; sIC: the staged per-interval constants.  Not inlined:
+// the staged y.  e = {record index r in the strip | pixel t in the strip << 16,
+// f of the pixel (the quadratic kinds)}; the record holds the unscaled point
+// (y0, h0) = (v, z) / Delta until then; sIC: the staged per-interval constants.  Not inlined:
 // every record below the graph goes through this one compiled body, whichever
 // warp pass (or kernel) handles it, so its result does not depend on how the
 // records fall into passes.  Pp: the parameters, in shared memory.
 template <int KIND>
 __device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, const float4 *sIC,
-                                           int pix0, int4 e)
+                                           int pix0, int2 e)
 {
     const LiftParams &P = *Pp;
-    const int r = e.x, pp = e.y;
+    const int r = e.x & 0xffff, pp = pix0 + (e.x >> 16);
     const int i = r - (pp - pix0) * P.k;
     float2 *rec = reinterpret_cast<float2 *>(sY + r);
     const float2 p0 = rec[0];
@@ -330,7 +330,7 @@ __device__ __noinline__ void strip_project(const LiftParams *Pp, float4 *sY, con
     if (KIND == 2) {
         piece_project_below<2>(P, pp, i, l, p0.x, p0.y, yo, ho);
     } else {
-        const QPiece qp = make_qpiece_f(P, __int_as_float(e.z), l, l + P.delta);
+        const QPiece qp = make_qpiece_f(P, __int_as_float(e.y), l, l + P.delta);
         qpiece_project(qp, p0.x, p0.y, yo, ho);
     }
     rec[0] = make_float2(P.delta * yo, P.delta * ho);
@@ -378,9 +378,10 @@ __device__ __forceinline__ bool strip_record(const LiftParams &P, float4 *sY, co
 }
 
 // A warp's ring of queued records: entries [head, head + cnt) (mod 64), each
-// {record, pixel, f of the pixel, unused}.
+// {record | pixel in the strip << 16, f of the pixel} (records and pixels of
+// a strip fit in 16 bits: at most 256 pixels and 64 intervals).
 struct StripRing {
-    int4 *e;
+    int2 *e;
     int head, cnt;
 };
 
@@ -394,7 +395,7 @@ __device__ __forceinline__ void strip_queue(StripRing &R, bool below, int r, int
     const unsigned m = __ballot_sync(0xffffffffu, below);
     if (below)
         R.e[(R.head + R.cnt + __popc(m & ((1u << lane) - 1u))) & 63] =
-            make_int4(r, pix, __float_as_int(fv), 0);
+            make_int2(r | ((pix - pix0) << 16), __float_as_int(fv));
     R.cnt += __popc(m);
     if (R.cnt >= 32) {
         __syncwarp();
@@ -486,12 +487,15 @@ __device__ __forceinline__ float strip_chunk_any(const LiftParams &P, const Lift
 // state pointers given, the pixels [p0, p1) in strips of blockDim.x / T) or of
 // a batch (strip blockIdx.x belongs to instance strip_inst[blockIdx.x], whose
 // descriptor is D[...]; strips of instances whose live flag is 0 return).
+// A single problem reads y1, q1 and writes the updated y, q to yout1, qout1:
+// the same arrays for the solver's in-place step, the next stored state's for
+// the recomputation of the unrolled solve (the arithmetic is the same).
 template <int KIND>
 __global__ void __launch_bounds__(256, 4)
-dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 *__restrict__ y1,
-                  float *__restrict__ q1, int p0, int p1, const InstDesc *__restrict__ D,
-                  const int *__restrict__ strip_inst, const int *__restrict__ live, int *err,
-                  int ahead)
+dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, const float4 *y1,
+                  const float *__restrict__ q1, float4 *yout1, float *qout1, int p0, int p1,
+                  const InstDesc *__restrict__ D, const int *__restrict__ strip_inst,
+                  const int *__restrict__ live, int *err, int ahead)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ LiftParams sP;
@@ -502,8 +506,10 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     // there) and, for the projections, in shared memory
     LiftParams P;
     const float2 *xbar;
-    float4 *y;
-    float *q;
+    const float4 *y;
+    const float *q;
+    float4 *yout;
+    float *qout;
     int s;
     if (D == nullptr) {
         if (P1.live && *P1.live == 0) return;
@@ -511,14 +517,18 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
         xbar = xbar1;
         y = y1;
         q = q1;
+        yout = yout1;
+        qout = qout1;
         s = blockIdx.x;
     } else {
         const int inst = strip_inst[blockIdx.x];
         if (!live[inst]) return;
         P = D[inst].P;
         xbar = D[inst].S.xbar;
-        y = D[inst].S.y;
-        q = D[inst].S.q;
+        yout = D[inst].S.y;
+        qout = D[inst].S.q;
+        y = yout;
+        q = qout;
         s = blockIdx.x - D[inst].strip0;
         p0 = 0;
         p1 = P.N;
@@ -534,8 +544,8 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     const int spp = blockDim.x >> tshift;
     const StripSmem L = strip_smem(spp, k, blockDim.x);
     float4 *sIC = reinterpret_cast<float4 *>(smem + L.ic_off);
-    int4 *sRing = reinterpret_cast<int4 *>(smem + L.ring_off) + warp * 64;
-    int4 *sPool = reinterpret_cast<int4 *>(smem + L.pool_off);
+    int2 *sRing = reinterpret_cast<int2 *>(smem + L.ring_off) + warp * 64;
+    int2 *sPool = reinterpret_cast<int2 *>(smem + L.pool_off);
     uint64_t *bar = &s_bar;
 
     // where the strip lies (record indices fit in int: N*k < 2^31; pixels are
@@ -623,7 +633,7 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
                                    stp.z, lane);
     }
     // thread 0 of the pixel ends with the sum of sbar over all intervals
-    if (act && j == 0) q[pix] = qo - stp.y * (1.0f + P.delta * tail);
+    if (act && j == 0) qout[pix] = qo - stp.y * (1.0f + P.delta * tail);
 
     // the warps' left-overs (fewer than 32 each) into the CTA's pool, then
     // projected in passes of 32 spread over the warps
@@ -639,7 +649,7 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
     fence_proxy_async_smem();                  // the records written above ...
     __syncthreads();
     if (tid == 0) {                            // ... go back by one bulk store
-        bulk_store(y + ya, sY, static_cast<uint32_t>(n) * k * 16);
+        bulk_store(yout + ya, sY, static_cast<uint32_t>(n) * k * 16);
         bulk_store_commit();
         bulk_wait_read();                      // the shared memory may then go
     }
@@ -657,9 +667,12 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, float4 
 // and tbase + (2b + 1) ppb (tbase <= p0; pixels before p0 are idle).
 // ahead > 0 (images): thread 0 also prefetches into L2 the records of block
 // blockIdx.x + ahead, the block that takes this one's place on the SM.
+// x_out: where the new x goes (x itself for the solver's in-place step, the
+// next stored state's x for the recomputation of the unrolled solve).
 template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
-primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restrict__ xbar,
+primal_step_kernel(const LiftParams P, const float2 *__restrict__ x, float2 *x_out,
+                   float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q,
                    const float *__restrict__ pz, int tbase, int p0, int p1, int ahead)
 {
@@ -732,7 +745,7 @@ primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *__restric
         const float un = fminf(fmaxf(xo[u].x - tau_u * (d[u].x - dv), 0.0f), 1.0f);
         const float sn =
             xo[u].y - ic.y * (d[u].y - P.delta * qq[u] + P.delta * head - ic.x * d[u].x);
-        x[o[u]] = make_float2(un, sn);
+        x_out[o[u]] = make_float2(un, sn);
         xbar[o[u]] = make_float2(2.0f * un - xo[u].x, 2.0f * sn - xo[u].y);
     }
 }
@@ -842,8 +855,8 @@ cudaError_t launch_batch_iteration(int threads, const InstDesc *D, const int *ti
         cudaError_t e = strip_occupancy<0>(G.threads, G.bytes, &resident);
         if (e != cudaSuccess) return e;
         LiftParams none{};
-        dual_strip_kernel<0><<<G.nstrips, G.threads, G.bytes, st>>>(none, nullptr, nullptr, nullptr,
-                                                                   0, 0, D, G.strip_inst, live, err, 0);
+        dual_strip_kernel<0><<<G.nstrips, G.threads, G.bytes, st>>>(
+            none, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, D, G.strip_inst, live, err, 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -882,9 +895,11 @@ void strip_shape_of(int k, int *threads, int *bytes, int *pixels)
     *bytes = strip_smem(spp, k, *threads).bytes;
 }
 
+// The dual step of the pixels [p0, p1) in strips: reads S, writes y and q to
+// yout, qout (S.y, S.q for the in-place step).
 template <int KIND>
 static cudaError_t launch_strips(const LiftParams &P, const LiftState &S, int p0, int p1,
-                                 cudaStream_t st)
+                                 cudaStream_t st, float4 *yout = nullptr, float *qout = nullptr)
 {
     const int spp = strip_spp(P.k);
     const int nstrips = (p1 - p0 + spp - 1) / spp;
@@ -897,8 +912,9 @@ static cudaError_t launch_strips(const LiftParams &P, const LiftState &S, int p0
     int resident = 0;
     const cudaError_t e = strip_occupancy<KIND>(threads, bytes, &resident);
     if (e != cudaSuccess) return e;
-    dual_strip_kernel<KIND><<<nstrips, threads, bytes, st>>>(P, S.xbar, S.y, S.q, p0, p1, nullptr,
-                                                            nullptr, nullptr, P.err, resident);
+    dual_strip_kernel<KIND><<<nstrips, threads, bytes, st>>>(
+        P, S.xbar, S.y, S.q, yout ? yout : S.y, qout ? qout : S.q, p0, p1, nullptr, nullptr,
+        nullptr, P.err, resident);
     return cudaGetLastError();
 }
 
@@ -973,19 +989,39 @@ cudaError_t launch_primal_range(const LiftParams &P, const LiftState &S, int p0,
     const int tbase = p0 - r;
     const int nb = (p1 - tbase + 2 * P.ppb - 1) / (2 * P.ppb);
     if (P.D > 1) {
-        primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, S.pz,
-                                                                     tbase, p0, p1, 0);
+        primal_step_kernel<true, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.x, S.xbar, S.y, S.q,
+                                                                     S.pz, tbase, p0, p1, 0);
         return cudaGetLastError();
     }
     int ahead = 0;
     const cudaError_t e = primal_resident(&ahead);
     if (e != cudaSuccess) return e;
     if (P.live != nullptr)
-        primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
-                                                                     tbase, p0, p1, ahead);
+        primal_step_kernel<false, true><<<nb, kStepThreads, 0, st>>>(P, S.x, S.x, S.xbar, S.y, S.q,
+                                                                     nullptr, tbase, p0, p1, ahead);
     else
-        primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.xbar, S.y, S.q, nullptr,
-                                                                      tbase, p0, p1, ahead);
+        primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, S.x, S.x, S.xbar, S.y, S.q,
+                                                                      nullptr, tbase, p0, p1, ahead);
+    return cudaGetLastError();
+}
+
+// One iteration from the state Sin into the state Sout (images, quadratic
+// kinds): the dual step reads Sin's xbar, y, q and writes Sout's y, q; the
+// primal step reads Sin's x and Sout's y, q and writes Sout's x, xbar.  The
+// same kernels and arithmetic as the in-place iteration, so the result is
+// bitwise the same; Sin is left unchanged.
+cudaError_t launch_iteration_into(const LiftParams &P, const LiftState &Sin, const LiftState &Sout,
+                                  cudaStream_t st)
+{
+    if (P.D != 1 || P.kind == 2 || P.live != nullptr) return cudaErrorInvalidValue;
+    cudaError_t e = launch_strips<0>(P, Sin, 0, P.N, st, Sout.y, Sout.q);
+    if (e != cudaSuccess) return e;
+    const int nb = (P.N + 2 * P.ppb - 1) / (2 * P.ppb);
+    int ahead = 0;
+    e = primal_resident(&ahead);
+    if (e != cudaSuccess) return e;
+    primal_step_kernel<false, false><<<nb, kStepThreads, 0, st>>>(P, Sin.x, Sout.x, Sout.xbar, Sout.y,
+                                                                  Sout.q, nullptr, 0, 0, P.N, ahead);
     return cudaGetLastError();
 }
 
