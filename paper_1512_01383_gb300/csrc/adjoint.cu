@@ -4,8 +4,9 @@
 // respect to the data f, lambda, alpha and nu.  Not part of the paper; it
 // differentiates the map of pdhg_step.cu (Sec. 4) exactly, including the
 // clamp of u, the l2-ball projection (Prop. 5) and the epigraph projections
-// (Fig. 7), whose local Jacobians come from the same piece / projection code
-// evaluated on forward-mode dual numbers (lift_ad.cuh).
+// (Fig. 7), whose local Jacobians are written out per branch of the
+// projection (ray, kink, parabola arc), with the envelope's dependence on the
+// data-term parameters taken from forward-mode dual numbers (lift_ad.cuh).
 //
 // With x = (u, s), xbar, y = (v, z, px, py), q and adjoints ax, axb, ay, aq,
 // one reverse iteration is two kernels:
@@ -93,33 +94,122 @@ __device__ __forceinline__ float div_p(const LiftParams &P, const float4 *__rest
 }
 
 // The epigraph projection of a record below the graph of rho_i^*, pulled
-// back: (y0, h0) = (v^, z^)/Delta, the adjoint (ax, ay) of the projected
+// back: (y0, h0) = (v^, z^)/Delta, the adjoint (gy, gh) of the projected
 // (v', z') = Delta (yo, ho), the pixel's f and the interval's left label l.
 // Returns the adjoint of (v^, z^) in (av, az), and Delta times the adjoint's
-// derivative with respect to f, alpha and nu in df, dga, dgn: the piece and
-// projection code of the forward step evaluated on dual numbers seeded in
-// (y0, h0, f, alpha, nu).
-__device__ __forceinline__ void epi_pullback(const LiftParams &P, float y0v, float h0v, float ax,
-                                             float ay, float fv, float l, float &av, float &az,
+// derivative with respect to f, alpha and nu in df, dga, dgn.
+//
+// The branch (ray, kink or arc) is the one the forward step's float code
+// takes; its derivative is written out for that branch, with
+// L = gy yo + gh ho:
+//   ray of slope l:  yo = (y0 + l (h0 + A)) / (1 + l^2), ho = l yo - A, so
+//                    with G = (gy + gh l)/(1 + l^2): dL/dy0 = G,
+//                    dL/dh0 = G l, dL/dA = G l - gh (the right ray: r, B);
+//   kink at m1:      (yo, ho) = (m1, l m1 - A): dL/dm1 = gy + gh l,
+//                    dL/dA = -gh (the right kink: m2, r, B);
+//   parabola arc:    yo = a d, ho = a d (c + d/2) with d the root of the
+//                    cubic F(d) = d^3 + 3c d^2 + (2 + 2c^2 - 2h0/a) d
+//                    - 2(c h0 + y0)/a of the stationarity condition, so by
+//                    the implicit-function theorem dd = -(dF at fixed d) / F'(d):
+//                    with mu = (dL/dd) / F'(d), dL/dy0 = 2 mu / a,
+//                    dL/dh0 = 2 mu (d + c)/a, and the partials of F in c and a
+//                    (a root clamped to an end of the arc follows that end).
+// The piece's own parameters (a, c, A, B, m1, m2, t1, t2) depend on f, alpha
+// and nu through the envelope construction of lift_device.cuh, evaluated here
+// on dual numbers seeded in those three.
+__device__ __forceinline__ void epi_pullback(const LiftParams &P, float y0, float h0, float gy,
+                                             float gh, float fv, float l, float &av, float &az,
                                              float &df, float &dga, float &dgn)
 {
-    using D5 = Dual<5>;
-    const D5 y0 = D5::seed(y0v, 0), h0 = D5::seed(h0v, 1);
-    const D5 f = D5::seed(fv, 2), al = D5::seed(P.alpha, 3), nu = D5::seed(P.nu, 4);
+    using D3 = Dual<3>;
     const float r = l + P.delta;
-    QPieceT<D5> qp;
+    const QPiece q = make_qpiece_f(P, fv, l, r);   // the forward step's float piece
+    av = gy;
+    az = gh;
+    df = dga = dgn = 0.0f;
+    if (h0 >= qpiece_conj(q, y0)) return;           // in the epigraph: identity
+    // adjoints of the piece's parameters
+    float La = 0.0f, Lc = 0.0f, LA = 0.0f, LB = 0.0f, Lm1 = 0.0f, Lm2 = 0.0f, Lt1 = 0.0f,
+          Lt2 = 0.0f;
+    const float ph1 = q.l * q.m1 - q.A;
+    const float e1 = fmaxf(ph1 - h0, 0.0f);
+    const float ph2 = q.r * q.m2 - q.B;
+    const float e2 = fmaxf(ph2 - h0, 0.0f);
+    if (q.m1 - y0 + e1 * q.l > 0.0f) {              // left ray
+        const float G = (gy + gh * q.l) / (1.0f + q.l * q.l);
+        av = G;
+        az = G * q.l;
+        LA = G * q.l - gh;
+    } else if (q.m2 - y0 + e2 * q.r < 0.0f) {       // right ray
+        const float G = (gy + gh * q.r) / (1.0f + q.r * q.r);
+        av = G;
+        az = G * q.r;
+        LB = G * q.r - gh;
+    } else if (!q.arc || q.m1 - y0 + e1 * q.t1 >= 0.0f) {   // left kink
+        av = az = 0.0f;
+        Lm1 = gy + gh * q.l;
+        LA = -gh;
+    } else if (q.m2 - y0 + e2 * q.t2 <= 0.0f) {     // right kink
+        av = az = 0.0f;
+        Lm2 = gy + gh * q.r;
+        LB = -gh;
+    } else {                                        // parabola arc
+        const float ia = 1.0f / q.a;
+        const float p = 2.0f - q.c * q.c - 2.0f * h0 * ia;
+        const float qq = -2.0f * (q.c + y0 * ia);
+        const float sg = qq <= 0.0f ? 1.0f : -1.0f;
+        float w = sg * cubic_outer_root(p, fabsf(qq));
+        int wend = 0;                               // 1, 2: w clamped to t1, t2
+        if (!(w >= q.t1)) { w = q.t1; wend = 1; }
+        if (!(w <= q.t2)) { w = q.t2; wend = 2; }
+        float d = w - q.c;
+        const float b2 = 3.0f * q.c;
+        const float b1 = 2.0f + 2.0f * q.c * q.c - 2.0f * h0 * ia;
+        const float b0 = -2.0f * (q.c * h0 + y0) * ia;
+        const float F = ((d + b2) * d + b1) * d + b0;
+        const float dF = (3.0f * d + 2.0f * b2) * d + b1;
+        int dend = -1;                              // -1: no Newton step; 0: interior root
+        if (dF > 0.0f) {
+            float v = d - F / dF;
+            dend = 0;
+            if (!(v >= q.t1 - q.c)) { v = q.t1 - q.c; dend = 1; }
+            if (!(v <= q.t2 - q.c)) { v = q.t2 - q.c; dend = 2; }
+            d = v;
+        }
+        const float Ld = q.a * (gy + gh * (q.c + d));   // dL/dd
+        La = d * (gy + gh * (q.c + 0.5f * d));          // direct dependence on a
+        Lc = gh * q.a * d;                               // ... and on c
+        av = az = 0.0f;
+        if (dend == 0) {
+            float Fd = (3.0f * d + 6.0f * q.c) * d + b1;     // F'(d) at the root
+            if (!(Fd > 0.0f)) Fd = dF;
+            const float mu = Ld / Fd;
+            av = 2.0f * mu * ia;
+            az = 2.0f * mu * (d + q.c) * ia;
+            Lc -= mu * ((3.0f * d + 4.0f * q.c) * d - 2.0f * h0 * ia);
+            La -= mu * 2.0f * (h0 * d + q.c * h0 + y0) * ia * ia;
+        } else {
+            const int end = dend > 0 ? dend : wend;     // d = t - c for the end t
+            if (end == 1) Lt1 += Ld;
+            if (end == 2) Lt2 += Ld;
+            Lc -= Ld;
+        }
+    }
+    // through the envelope construction to (f, alpha, nu)
+    QPieceT<D3> Q;
+    const D3 f3 = D3::seed(fv, 0), al = D3::seed(P.alpha, 1), nu = D3::seed(P.nu, 2);
     if (P.kind == 3)
-        qp = make_quad_piece<D5>(al, f + (periodic_center(f.v, P.nu, l, r) - f.v), l, r);
-    else if (P.kind == 0) qp = make_quad_piece<D5>(al, f, l, r);
-    else qp = make_trunc_piece<D5>(al, nu, tsqrt(nu / al), f, l, r);
-    D5 yo, ho;
-    qpiece_project(qp, y0, h0, yo, ho);
-    // (v', z') = Delta (yo, ho)((v^, z^)/Delta)
-    av = ax * yo.d[0] + ay * ho.d[0];
-    az = ax * yo.d[1] + ay * ho.d[1];
-    df = P.delta * (ax * yo.d[2] + ay * ho.d[2]);
-    dga = P.delta * (ax * yo.d[3] + ay * ho.d[3]);
-    dgn = P.delta * (ax * yo.d[4] + ay * ho.d[4]);
+        Q = make_quad_piece<D3>(al, f3 + (periodic_center(fv, P.nu, l, r) - fv), l, r);
+    else if (P.kind == 0) Q = make_quad_piece<D3>(al, f3, l, r);
+    else Q = make_trunc_piece<D3>(al, nu, tsqrt(nu / al), f3, l, r);
+    float g[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        g[j] = La * Q.a.d[j] + Lc * Q.c.d[j] + LA * Q.A.d[j] + LB * Q.B.d[j] + Lm1 * Q.m1.d[j] +
+               Lm2 * Q.m2.d[j] + Lt1 * Q.t1.d[j] + Lt2 * Q.t2.d[j];
+    df = P.delta * g[0];
+    dga = P.delta * g[1];
+    dgn = P.delta * g[2];
 }
 
 }  // namespace
@@ -159,10 +249,9 @@ adj_primal_local_kernel(const LiftParams P, const float2 *__restrict__ x_n,
 }
 
 // ---------------------------------------------------------------------------
-// Four blocks per SM (64 registers, a few bytes spilled): the dual-number
-// projection below otherwise holds 80 registers and leaves three.  Records in
-// the epigraph of rho_i^* (the forward step's float test) take its identity
-// Jacobian; those below it are packed per warp into one dual-number pass.
+// Four blocks per SM (64 registers).  Records in the epigraph of rho_i^* (the
+// forward step's float test) take its identity Jacobian; those below it are
+// packed per warp into one pass of the projection's pullback.
 template <int KIND>
 __global__ void __launch_bounds__(kAdjThreads, 4)
 adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
@@ -175,7 +264,7 @@ adj_dual_local_kernel(const LiftParams P, const float2 *__restrict__ xbar_n,
     __shared__ float2 s_la[kAdjThreads / 32], s_lb[kAdjThreads / 32];
     __shared__ double red[3][kAdjThreads / 32];
     // per warp: the records below the graph of rho_i^*, packed for the
-    // dual-number projection, and its results for their owners
+    // projection's pullback, and its results for their owners
     __shared__ float4 s_qa[kAdjThreads / 32][32];   // {y0, h0, a.x, a.y}
     __shared__ float2 s_qb[kAdjThreads / 32][32];   // {f, gamma_i}
     __shared__ float4 s_qr[kAdjThreads];            // {adj_v, adj_z, df, -} by owner
