@@ -431,10 +431,10 @@ def run_volume(G, torch, stream, dev, D=128, L=8, iters=200):
                                           "seconds": dt, "rel_gap": gap}}
 
 
-def run_differentiable(G, torch, stream, dev, iters=500, every=50):
+def run_differentiable(G, torch, stream, dev, iters=500, every=50, reps=3):
     """Unrolled solve for differentiation: 256x256 truncated quadratic, L=16,
     500 iterations, checkpoints every 50; forward (checkpointed) and the
-    hand-written reverse pass."""
+    hand-written reverse pass (best of `reps` runs)."""
     from paper_1512_01383_gb300 import synth
     noisy, clean = synth.voronoi_ramps(256, 256, synth.BASE_SEED + 4)
     f = torch.from_numpy(synth.as_f32(noisy)).to(dev)
@@ -444,7 +444,7 @@ def run_differentiable(G, torch, stream, dev, iters=500, every=50):
         u = torch.empty((256, 256), device=dev)
         gf = torch.empty_like(u)
         res = []
-        for _ in range(3):
+        for _ in range(reps):
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             torch.cuda.synchronize()
             e0.record(stream)
@@ -706,7 +706,20 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the ROF, stereo, differentiable, phase, baseline-lifting and volume "
                          "sections")
+    ap.add_argument("--only", choices=["differentiable"],
+                    help="run one section alone and print its JSON (differentiable: the "
+                         "256x256, L=16 unrolled solve and its reverse pass)")
+    ap.add_argument("--iters", type=int, default=500,
+                    help="unrolled iterations of --only differentiable")
     args = ap.parse_args()
+    if args.only == "differentiable":
+        import torch
+        from paper_1512_01383_gb300 import lift as G
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.current_stream(dev)
+        print(json.dumps(run_differentiable(G, torch, stream, dev, iters=args.iters,
+                                            reps=max(args.steps, 1))))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.warmup < 3:

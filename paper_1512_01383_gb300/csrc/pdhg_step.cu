@@ -283,6 +283,14 @@ __host__ __device__ inline StripSmem strip_smem(int spp, int k, int threads)
 // records land on aligned shared addresses.  A first record that sits 8 bytes
 // past a boundary and a last record that starts on one (an 8-byte tail) are
 // plain loads.
+// L2 prefetch of the 16-byte aligned part of the floats [p, p + n).
+__device__ __forceinline__ void prefetch_l2_aligned(const float *p, int n)
+{
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    const uintptr_t e = reinterpret_cast<uintptr_t>(p + n) & ~uintptr_t(15);
+    if (e > a) bulk_prefetch_l2(reinterpret_cast<const void *>(a), static_cast<uint32_t>(e - a));
+}
+
 struct XRange {
     int a, e, s, e2;   // range, and its bulk part [s, e2) (empty if e2 <= s)
     int ph;            // 1: record a sits 8 bytes past a 16-byte boundary
@@ -579,6 +587,10 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, const f
             bulk_prefetch_l2(y + q0 * k, static_cast<uint32_t>(nq) * k * 16);
             const XRange RQ = x_range(xbar, q0 * k, clip(q0 + nq + 1LL) * k);
             if (RQ.e2 > RQ.s) bulk_prefetch_l2(xbar + RQ.s, (RQ.e2 - RQ.s) * 8);
+            // and its f and q, read with plain loads once the copies land
+            // (the 16-byte aligned part of each run)
+            if (KIND != 2) prefetch_l2_aligned(P.f + q0, nq);
+            prefetch_l2_aligned(q + q0, nq);
         }
     } else if (tid == (blockDim.x > 32 ? 32 : 1)) {   // another warp if there is one
         x_ragged(RX, xbar, sX);
@@ -671,7 +683,7 @@ dual_strip_kernel(const LiftParams P1, const float2 *__restrict__ xbar1, const f
 // next stored state's x for the recomputation of the unrolled solve).
 template <bool VOL, bool LIVE>
 __global__ void __launch_bounds__(kStepThreads)
-primal_step_kernel(const LiftParams P, const float2 *__restrict__ x, float2 *x_out,
+primal_step_kernel(const LiftParams P, float2 *__restrict__ x, float2 *x_out,
                    float2 *__restrict__ xbar,
                    const float4 *__restrict__ y, const float *__restrict__ q,
                    const float *__restrict__ pz, int tbase, int p0, int p1, int ahead)
@@ -691,6 +703,7 @@ primal_step_kernel(const LiftParams P, const float2 *__restrict__ x, float2 *x_o
             const uintptr_t xe = reinterpret_cast<uintptr_t>(x + e * P.k) & ~uintptr_t(15);
             if (xe > xa)
                 bulk_prefetch_l2(reinterpret_cast<const void *>(xa), static_cast<uint32_t>(xe - xa));
+            prefetch_l2_aligned(q + a, static_cast<int>(e - a));
         }
     }
     int lp, i;

@@ -58,3 +58,23 @@ def test_truncated_chain_closed_form(row):
     assert D <= E + 1e-9 and Ph >= E - 1e-9
     for v in (Ph, D, Enc):
         assert abs(v - E) <= 1e-7, (v, E)
+
+
+PL_COSTS = np.array([[3.0, 1.0, 0.0, 1.0, 3.0], [0.0, 1.5, 3.0, 4.5, 6.0]])
+
+
+@pytest.mark.parametrize("row", list(golden("pl_two_pixel.txt")))
+def test_pl_two_pixel_closed_form(row):
+    """Sampled (piecewise-linear) costs (Sec. 5.4) on two pixels at L = 2
+    (Prop. 3): at convergence the unlifted pair is the hand-derived optimum
+    and P, D and the nonconvex E_nc all meet its energy."""
+    lam, u1, u2, E = row
+    P = O.Problem(O.PL, 1, 2, 2, 0.0, 4.0, lam=lam, cost=PL_COSTS, smin=0.0, smax=4.0)
+    X = O.State(P)
+    O.pdhg(P, X, 20000)
+    ut = O.unlift(P, X.u)
+    assert np.abs(ut - [u1, u2]).max() <= 1e-7, ut
+    Ph, D, Enc = O.energy(P, X)
+    assert D <= E + 1e-9 and Ph >= E - 1e-9
+    for v in (Ph, D, Enc):
+        assert abs(v - E) <= 1e-7, (v, E)

@@ -35,17 +35,26 @@ def _gpu_grads(s, iters, every, clean):
     return u.cpu().numpy(), gf.cpu().numpy(), np.array(sc)
 
 
-@pytest.mark.parametrize("kind,L,lam,alpha,nu,theta,aniso", [
+CASES = [
     (1, 5, 0.25, 25.0, 0.1, 1.0, 0),
     (0, 4, 0.2, 1.5, 0.0, 1.0, 0),
     (1, 9, 0.3, 20.0, 0.08, 1.0, 0),
     (1, 5, 0.25, 25.0, 0.1, 16.0, 0),
     (1, 5, 0.25, 25.0, 0.1, 1.0, 1),
     (3, 6, 0.2, 1.5, 0.4, 1.0, 0),      # periodic pieces, period 0.4 on [0, 1]
+]
+
+
+@pytest.mark.parametrize("H,W,iters,df_tol,sc_tol", [
+    # observed on a GB300: dL/df within 4.7e-6 of its maximum and the
+    # scalars within 1.7e-3 (11 x 9), 3.3e-4 and 3.9e-4 (32 x 32)
+    (11, 9, 30, 1e-4, 5e-3),
+    (32, 32, 100, 1e-3, 2e-3),
 ])
-def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, aniso):
+@pytest.mark.parametrize("kind,L,lam,alpha,nu,theta,aniso", CASES)
+def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, aniso, H, W, iters,
+                                             df_tol, sc_tol):
     _require_gpu()
-    H, W, iters = 11, 9, 30
     noisy, clean = synth.voronoi_ramps(H, W, 81 + L, cells=4)
     f = synth.as_f32(noisy)
     with _solver(kind, f, L, lam, alpha, nu, theta, aniso) as s:
@@ -60,12 +69,12 @@ def test_gradients_match_oracle_reverse_pass(kind, L, lam, alpha, nu, theta, ani
     gfo, gso = O.unrolled_grad(P, iters, 2.0 * (uo - clean.reshape(-1)))
     scale = np.abs(gfo).max()
     assert scale > 1e-3
-    assert np.abs(gf.reshape(-1) - gfo).max() <= 2e-3 * scale
+    assert np.abs(gf.reshape(-1) - gfo).max() <= df_tol * scale
     # the unrolled map is piecewise smooth: where an FP32 and an FP64 branch
     # choice differ near a region boundary the one-sided derivatives differ,
-    # so the scalar sums over all records get a 1 % tolerance
+    # which the scalar sums over all records collect
     for g, o in zip(gs, gso):
-        assert abs(g - o) <= 1e-2 * max(abs(o), 1e-2), (gs, gso)
+        assert abs(g - o) <= sc_tol * max(abs(o), 1e-2), (gs, gso)
 
 
 def test_checkpoint_spacing_does_not_change_gradients():

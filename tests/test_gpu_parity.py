@@ -479,3 +479,25 @@ def test_truncated_chain_golden(resident):
         assert np.abs(ut - want).max() <= 2e-6, (ut, want)
         for v in (Pg, Dg, Eg):
             assert abs(v - E) <= 1e-6, (v, E)
+
+
+@pytest.mark.parametrize("resident", [True, False])
+def test_pl_two_pixel_golden(resident):
+    """The hand-derived sampled-cost pairs of tests/golden/pl_two_pixel.txt
+    (Sec. 5.4 costs, L = 2, Prop. 3) on the GPU: after 20 000 iterations the
+    unlifted pair meets them within FP32 rounding of labels on [0, 4], and the
+    energies within the stated relative bar (FP32 rounding of u on [0, 4],
+    times cost slopes up to 2, is about 2e-6 of the energy)."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    from test_golden import PL_COSTS, golden
+    cost = torch.tensor(PL_COSTS.reshape(1, 2, 5), dtype=torch.float32, device="cuda")
+    for lam, u1, u2, E in golden("pl_two_pixel.txt"):
+        with G.Solver(G.LIFT_PL_SAMPLED, 1, 2, 2, 0.0, 4.0, lam, 0.0, 0.0, cost=cost,
+                      sample_min=0.0, sample_max=4.0, resident=resident) as s:
+            s.iterate(20000)
+            ut = s.unlift().reshape(-1)
+            Pg, Dg, Eg = s.energy()
+        assert np.abs(ut - [u1, u2]).max() <= 4 * 2e-6, (ut, u1, u2)
+        for v in (Pg, Dg, Eg):
+            assert abs(v - E) <= E_TOL * max(abs(E), 1.0), (v, E)
