@@ -78,3 +78,23 @@ def test_pl_two_pixel_closed_form(row):
     assert D <= E + 1e-9 and Ph >= E - 1e-9
     for v in (Ph, D, Enc):
         assert abs(v - E) <= 1e-7, (v, E)
+
+
+@pytest.mark.parametrize("row", list(golden("periodic_two_pixel.txt")))
+def test_periodic_two_pixel_closed_form(row):
+    """Wrapped phases on either side of the wrap (Sec. 5.5) on two pixels:
+    at convergence the unlifted pair is the hand-derived unwrapped optimum,
+    and P, D and the nonconvex E_nc (the squared circular distance) all meet
+    its energy."""
+    L, lam, alpha, u1, u2, E = row
+    two_pi = 2 * np.pi
+    f = np.array([two_pi - 0.3, 0.3])
+    P = O.Problem(O.PERIODIC, 1, 2, int(L), 0.0, 2 * two_pi, lam=lam, alpha=alpha, nu=two_pi, f=f)
+    X = O.State(P)
+    O.pdhg(P, X, 40000)
+    ut = O.unlift(P, X.u)
+    assert np.abs(ut - [u1, u2]).max() <= 1e-7, ut
+    Ph, D, Enc = O.energy(P, X)
+    assert D <= E + 1e-9 and Ph >= E - 1e-9
+    for v in (Ph, D, Enc):
+        assert abs(v - E) <= 1e-7, (v, E)

@@ -501,3 +501,25 @@ def test_pl_two_pixel_golden(resident):
         assert np.abs(ut - [u1, u2]).max() <= 4 * 2e-6, (ut, u1, u2)
         for v in (Pg, Dg, Eg):
             assert abs(v - E) <= E_TOL * max(abs(E), 1.0), (v, E)
+
+
+@pytest.mark.parametrize("resident", [True, False])
+def test_periodic_two_pixel_golden(resident):
+    """The hand-derived unwrapped pairs of tests/golden/periodic_two_pixel.txt
+    (Sec. 5.5, L = 2 and 9) on the GPU: after 40 000 iterations the unlifted
+    pair meets them within FP32 rounding of labels on [0, 4 pi] (2e-6 of the
+    range), and the energies within the stated relative bar."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    from test_golden import golden
+    two_pi = 2 * np.pi
+    f = torch.tensor([[two_pi - 0.3, 0.3]], dtype=torch.float32, device="cuda")
+    for L, lam, alpha, u1, u2, E in golden("periodic_two_pixel.txt"):
+        with G.Solver(G.LIFT_PERIODIC_QUAD, 1, 2, int(L), 0.0, 2 * two_pi, lam, alpha, two_pi,
+                      f=f, resident=resident) as s:
+            s.iterate(40000)
+            ut = s.unlift().reshape(-1)
+            Pg, Dg, Eg = s.energy()
+        assert np.abs(ut - [u1, u2]).max() <= 2 * two_pi * 2e-6, (ut, u1, u2)
+        for v in (Pg, Dg, Eg):
+            assert abs(v - E) <= E_TOL * max(abs(E), 1.0), (v, E)
