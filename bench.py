@@ -56,8 +56,8 @@ PRIMAL_BYTES_PER_PIX = 40 * K_INT + 4
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid for the kernel sources
 # whose SHA-256 (of the files below, in this order) is DUAL_TRAFFIC_SRC; with
 # any other source the bench reports no traffic figure.
-DUAL_TRAFFIC_NCU = 149923328          # 121 714 688 read + 28 208 640 written
-DUAL_TRAFFIC_SRC = "27af94b52f122c6223bbc2ded9b171612036b33620be062bba95339a7308eb12"
+DUAL_TRAFFIC_NCU = 149552128          # 121 711 360 read + 27 840 768 written
+DUAL_TRAFFIC_SRC = "d59f2f9f478ad6d2d0ecded1a4797ea20a187dd638984fbe79cdc19ebcc62b7b"
 DUAL_KERNEL_FILES = ("pdhg_step.cu", "lift_device.cuh", "lift_bulk.cuh", "lift_params.h",
                      "lift_tile.cuh")
 
@@ -86,7 +86,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region.
+    Entering waits (at most 5 s) for the first sample, so nvidia-smi's own
+    start-up does not fall inside the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -95,6 +97,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.ready = threading.Event()
 
     def __enter__(self):
         try:
@@ -104,6 +107,7 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.ready.wait(timeout=5.0)
         except (FileNotFoundError, OSError):
             self.proc = None
         return self
@@ -111,6 +115,8 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.ready.set()
+        self.ready.set()
 
     def __exit__(self, *a):
         if self.proc:
