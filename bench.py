@@ -289,9 +289,9 @@ def run_stereo(G, torch, stream, dev, cap=60000, theta=0.1):
     sweep; the adaptive rule settles on worse balances here) to relative gap
     5e-2 and on to 1e-2, capped at `cap` iterations in all, with the mean
     |u~ - true disparity| at each stop.  On this piecewise-linear
-    (polyhedral, nowhere strongly convex) cost the gap falls about as 1/n
-    (halving per doubling of n), in FP64 as in FP32; 1e-3 would take about
-    a million iterations."""
+    (polyhedral, nowhere strongly convex) cost the bounds of the last
+    iterate oscillate and its gap stalls, in FP64 as in FP32, while bounds
+    taken at the average of the iterates keep closing."""
     from paper_1512_01383_gb300 import synth
     cost, disp = synth.stereo_cost(480, 640, synth.BASE_SEED + 3, ndisp=65)
     cd = torch.from_numpy(synth.as_f32(cost)).to(dev)

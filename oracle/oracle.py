@@ -373,3 +373,32 @@ def pdhg_adaptive(P: Problem, X: State, checks: int, every: int) -> float:
             th = min(max(th, 1e-4), 1e6)
             w *= 0.95
     return th
+
+
+def pdhg_averaged(P: Problem, X: State, iters: int, every: int = 1) -> State:
+    """Run ``iters`` iterations in place on X and return the uniform average
+    of the iterates after iterations every, 2 every, ... (u, s and the dual
+    v, z, p, q; the average's extrapolated point is its own x).  Every iterate
+    is feasible (u in [0,1]^k after the clamp, p_i in its ball, (v_i, z_i) in
+    the scaled epigraph after the projection), all three sets are convex, so
+    the average is feasible and P_hat and D evaluated at it bound the
+    relaxation's optimum as those of any iterate do."""
+    names = ("u", "s", "v", "z", "px", "py", "pz", "q")
+    acc = {n: np.zeros_like(getattr(X, n)) for n in names}
+    cnt = 0
+    done = 0
+    while done + every <= iters:
+        pdhg(P, X, every)
+        done += every
+        for n in names:
+            acc[n] += getattr(X, n)
+        cnt += 1
+    if done < iters:
+        pdhg(P, X, iters - done)
+    A = State(P)
+    if cnt:
+        for n in names:
+            getattr(A, n)[...] = acc[n] / cnt
+    A.ubar[...] = A.u
+    A.sbar[...] = A.s
+    return A
