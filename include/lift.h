@@ -229,6 +229,36 @@ int lift_gap(lift_handle h, double *rel_gap);
  * (on_host = 0, asynchronous) or a host pointer (on_host = 1). */
 int lift_unlift(lift_handle h, float *out, int on_host);
 
+/* Running average of the iterate, for bounds that the last iterate does not
+ * give on polyhedral problems (the sampled costs of Sec. 5.4: there the last
+ * iterate's dual bound keeps oscillating).  Every iterate is feasible (u in
+ * [0,1]^k, p_i in its ball of the set K of Prop. 5, (v_i, z_i) in the scaled
+ * epigraph of rho_i^*, eq. constraint_C) and these sets are convex, so the
+ * average is feasible and the energies of lift_energy evaluated at it bound
+ * the relaxation's optimum as well.
+ *
+ * lift_average(h, 1) adds the current iterate (x = {u, s}, the dual records
+ * y, and pz on a volume) to the average, a <- a + (x - a) / n for the n-th
+ * iterate added; the first call after creation or after lift_average(h, 0)
+ * sets a <- x.  lift_average(h, 0) empties the average (no device work).
+ * The averaged records live in the handle (allocated on the first
+ * accumulation: 24 bytes per (pixel, interval), 28 on a volume; LIFT_ERR_OOM
+ * if that fails) and are kept apart from the iterate, which the averaging
+ * never changes.  Asynchronous on the handle's stream.  LIFT_ERR_ARG for a
+ * band handle or accumulate other than 0 or 1. */
+int lift_average(lift_handle h, int accumulate);
+
+/* The number of iterates in the average (0 after lift_average(h, 0)); -1 for
+ * a null handle. */
+long long lift_average_count(lift_handle h);
+
+/* lift_energy and lift_unlift evaluated at the averaged iterate (same
+ * outputs, same synchronisation).  LIFT_ERR_ARG while the average is empty or
+ * for a band handle. */
+int lift_energy_average(lift_handle h, double *primal_relaxed, double *dual,
+                        double *e_nonconvex);
+int lift_unlift_average(lift_handle h, float *out, int on_host);
+
 /* State image for checkpoint / resume and for tests.  Layout (bytes, in
  * this order, all float32, pixel p = (z*H + y)*W + x, N = D*H*W, interval
  * i = 0..k-1):

@@ -72,6 +72,12 @@ struct lift_ctx {
     // the primal tile length, that the image's first pixel would have
     bool band = false;
     int halo_up = 0, halo_dn = 0, own0 = 0, own1 = 0, torg = 0;
+    // running average of the iterate (lift_average): x, y (and pz) records,
+    // allocated on the first accumulation; avg_count iterates in it
+    float2 *avg_x = nullptr;
+    float4 *avg_y = nullptr;
+    float *avg_pz = nullptr;
+    long long avg_count = 0;
 };
 
 namespace {
@@ -119,6 +125,9 @@ void free_ctx(lift_ctx *h)
     for (cudaEvent_t ev : h->band_e)
         if (ev) cudaEventDestroy(ev);
     if (h->prev) cudaFree(h->prev);
+    if (h->avg_x) cudaFree(h->avg_x);
+    if (h->avg_y) cudaFree(h->avg_y);
+    if (h->avg_pz) cudaFree(h->avg_pz);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
 }
@@ -760,6 +769,84 @@ int lift_energy(lift_handle h, double *primal_relaxed, double *dual, double *e_n
     if (dual) *dual = h->hout[1];
     if (e_nonconvex) *e_nonconvex = h->hout[2];
     if (!is_finite(h->hout[0]) || !is_finite(h->hout[1]) || !is_finite(h->hout[2])) return LIFT_ERR_NAN;
+    return LIFT_OK;
+}
+
+int lift_average(lift_handle h, int accumulate)
+{
+    if (!h || h->band || (accumulate != 0 && accumulate != 1)) return LIFT_ERR_ARG;
+    if (!accumulate) {
+        h->avg_count = 0;
+        return LIFT_OK;
+    }
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    if (!h->avg_x) {
+        int rc = dev_alloc(reinterpret_cast<void **>(&h->avg_x), Nk * sizeof(float2));
+        if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&h->avg_y), Nk * sizeof(float4));
+        if (rc == LIFT_OK && h->S.pz) rc = dev_alloc(reinterpret_cast<void **>(&h->avg_pz), Nk * sizeof(float));
+        if (rc != LIFT_OK) {
+            if (h->avg_x) cudaFree(h->avg_x);
+            if (h->avg_y) cudaFree(h->avg_y);
+            h->avg_x = nullptr;
+            h->avg_y = nullptr;
+            return rc;
+        }
+    }
+    const long long c = h->avg_count + 1;
+    LIFT_CK(lift::launch_average(h->S, h->avg_x, h->avg_y, h->avg_pz, Nk,
+                                 static_cast<float>(1.0 / static_cast<double>(c)), c == 1,
+                                 h->stream));
+    h->avg_count = c;
+    return LIFT_OK;
+}
+
+long long lift_average_count(lift_handle h)
+{
+    return h ? h->avg_count : -1;
+}
+
+// The handle's state with the averaged records in place of x, y (and pz).
+static int average_state(lift_handle h, lift::LiftState *Sa)
+{
+    if (!h || h->band || h->avg_count < 1) return LIFT_ERR_ARG;
+    *Sa = h->S;
+    Sa->x = h->avg_x;
+    Sa->xbar = h->avg_x;
+    Sa->y = h->avg_y;
+    Sa->pz = h->avg_pz;
+    return LIFT_OK;
+}
+
+int lift_energy_average(lift_handle h, double *primal_relaxed, double *dual, double *e_nonconvex)
+{
+    lift::LiftState Sa{};
+    const int rc = average_state(h, &Sa);
+    if (rc != LIFT_OK) return rc;
+    LIFT_CK(lift::launch_energy(h->P, Sa, h->partial, h->dout, h->stream));
+    LIFT_CK(cudaMemcpyAsync(h->hout, h->dout, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));
+    if (primal_relaxed) *primal_relaxed = h->hout[0];
+    if (dual) *dual = h->hout[1];
+    if (e_nonconvex) *e_nonconvex = h->hout[2];
+    if (!is_finite(h->hout[0]) || !is_finite(h->hout[1]) || !is_finite(h->hout[2])) return LIFT_ERR_NAN;
+    return LIFT_OK;
+}
+
+int lift_unlift_average(lift_handle h, float *out, int on_host)
+{
+    if (!out) return LIFT_ERR_ARG;
+    lift::LiftState Sa{};
+    const int rc = average_state(h, &Sa);
+    if (rc != LIFT_OK) return rc;
+    if (!on_host) {
+        LIFT_CK(lift::launch_unlift(h->P, Sa.x, out, h->stream));
+        return LIFT_OK;
+    }
+    LIFT_CK(lift::launch_unlift(h->P, Sa.x, h->ubuf, h->stream));
+    LIFT_CK(cudaMemcpyAsync(out, h->ubuf, h->N * sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream));
+    LIFT_CK(cudaStreamSynchronize(h->stream));
     return LIFT_OK;
 }
 

@@ -408,6 +408,53 @@ cudaError_t launch_envelope(const LiftParams &P, const int *pix, const int *inte
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Running average of the iterate: a <- a + w (x - a) record by record over
+// x = {u, s}, y = {v, z, px, py} (and pz on volumes); first: a <- x (the
+// average of one iterate; the buffers' old contents are not read).  A
+// grid-stride loop over the N*k records, one float2 and one float4 each.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+average_kernel(const float2 *__restrict__ x, const float4 *__restrict__ y,
+               const float *__restrict__ pz, float2 *__restrict__ ax, float4 *__restrict__ ay,
+               float *__restrict__ apz, size_t nk, float w, int first)
+{
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t r = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; r < nk;
+         r += stride) {
+        const float2 a = x[r];
+        const float4 b = y[r];
+        if (first) {
+            ax[r] = a;
+            ay[r] = b;
+            if (pz) apz[r] = pz[r];
+        } else {
+            const float2 c = ax[r];
+            const float4 d = ay[r];
+            ax[r] = make_float2(c.x + w * (a.x - c.x), c.y + w * (a.y - c.y));
+            ay[r] = make_float4(d.x + w * (b.x - d.x), d.y + w * (b.y - d.y),
+                                d.z + w * (b.z - d.z), d.w + w * (b.w - d.w));
+            if (pz) apz[r] = apz[r] + w * (pz[r] - apz[r]);
+        }
+    }
+}
+
+cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *apz, size_t nk,
+                           float w, bool first, cudaStream_t st)
+{
+    if (nk == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const size_t need = (nk + 255) / 256;
+    const size_t cap = static_cast<size_t>(sms) * 8;          // 8 blocks of 256 per SM
+    const unsigned blocks = static_cast<unsigned>(need < cap ? need : cap);
+    average_kernel<<<blocks, 256, 0, st>>>(S.x, S.y, apz ? S.pz : nullptr, ax, ay, apz, nk, w,
+                                           first ? 1 : 0);
+    return cudaGetLastError();
+}
+
 }  // namespace lift
 
 // ---------------------------------------------------------------------------

@@ -35,6 +35,7 @@ EXPORTED = (
     "lift_get_balance", "lift_set_resident", "lift_set_bands", "lift_unrolled_generation",
     "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
     "lift_cuda_error", "lift_batch_streams",
+    "lift_average", "lift_average_count", "lift_energy_average", "lift_unlift_average",
 )
 
 
@@ -83,6 +84,10 @@ def load(path: str = LIB_PATH):
         "lift_energy": (C.c_int, [vp, dp, dp, dp]),
         "lift_gap": (C.c_int, [vp, dp]),
         "lift_unlift": (C.c_int, [vp, vp, C.c_int]),
+        "lift_average": (C.c_int, [vp, C.c_int]),
+        "lift_average_count": (C.c_longlong, [vp]),
+        "lift_energy_average": (C.c_int, [vp, dp, dp, dp]),
+        "lift_unlift_average": (C.c_int, [vp, vp, C.c_int]),
         "lift_state_bytes": (C.c_size_t, [vp]),
         "lift_get_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
         "lift_set_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
@@ -263,6 +268,27 @@ def lift_unlift(h: int, out) -> None:
     _check(load().lift_unlift(C.c_void_p(h), C.c_void_p(p), on_host), "lift_unlift")
 
 
+def lift_average(h: int, accumulate: bool) -> None:
+    _check(load().lift_average(C.c_void_p(h), 1 if accumulate else 0), "lift_average")
+
+
+def lift_average_count(h: int) -> int:
+    return int(load().lift_average_count(C.c_void_p(h)))
+
+
+def lift_energy_average(h: int) -> tuple[float, float, float]:
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(load().lift_energy_average(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)),
+           "lift_energy_average")
+    return a.value, b.value, c.value
+
+
+def lift_unlift_average(h: int, out) -> None:
+    p, on_host = _ptr(out)
+    _check(load().lift_unlift_average(C.c_void_p(h), C.c_void_p(p), on_host),
+           "lift_unlift_average")
+
+
 def lift_state_bytes(h: int) -> int:
     return load().lift_state_bytes(C.c_void_p(h))
 
@@ -412,6 +438,26 @@ class Solver:
 
     def gap(self):
         return lift_gap(self.h)
+
+    def average_reset(self):
+        lift_average(self.h, False)
+
+    def average_add(self):
+        """Add the current iterate to the running average."""
+        lift_average(self.h, True)
+
+    def average_count(self) -> int:
+        return lift_average_count(self.h)
+
+    def energy_average(self):
+        return lift_energy_average(self.h)
+
+    def unlift_average(self, out=None) -> np.ndarray:
+        if out is None:
+            shape = (self.H, self.W) if self.D == 1 else (self.D, self.H, self.W)
+            out = np.empty(shape, dtype=np.float32)
+        lift_unlift_average(self.h, out)
+        return out
 
     @property
     def N(self) -> int:

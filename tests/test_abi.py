@@ -103,6 +103,10 @@ def test_null_arguments(lib):
     L.lift_batch_destroy(None)
     assert L.lift_set_bands(None, 0, None) == lib.LIFT_ERR_ARG
     assert L.lift_set_resident(None, 1, None) == lib.LIFT_ERR_ARG
+    assert L.lift_average(None, 1) == lib.LIFT_ERR_ARG
+    assert L.lift_average_count(None) == -1
+    assert L.lift_energy_average(None, None, None, None) == lib.LIFT_ERR_ARG
+    assert L.lift_unlift_average(None, None, 0) == lib.LIFT_ERR_ARG
 
 
 def test_volume_batch_rejected_before_any_cuda_call(lib):

@@ -1,0 +1,87 @@
+"""The running average of the iterate (lift_average, lift_energy_average,
+lift_unlift_average) against the oracle's average of the same iterates, and
+its edge cases.  Every iterate is feasible and the feasible set is convex, so
+the averaged point's energies are bounds of the relaxation too; on the
+sampled costs of Sec. 5.4 they close where the last iterate's do not."""
+import numpy as np
+import pytest
+
+import oracle as O
+from _cases import case, gpu_solver, oracle_run
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U_TOL = 1e-4       # unlifted image, normalised by (gamma_max - gamma_min)
+E_TOL = 1e-5       # energies, relative
+
+
+def _require_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+@pytest.mark.parametrize("kind,H,W,L", [(1, 19, 23, 5), (2, 17, 21, 6), (0, 24, 31, 3)])
+def test_average_matches_oracle(kind, H, W, L):
+    """Iterations 1..20 unaveraged, then the average of iterates 21..60 on
+    both sides: energies at the average within E_TOL, its unlifted image
+    within U_TOL of the label range."""
+    _require_gpu()
+    c = case(kind, H, W, L, 2100 + 10 * kind + L)
+    P, X = oracle_run(c, 20)
+    A = O.pdhg_averaged(P, X, 40)
+    with gpu_solver(c) as s:
+        s.iterate(20)
+        s.average_reset()
+        for _ in range(40):
+            s.iterate(1)
+            s.average_add()
+        assert s.average_count() == 40
+        eg = s.energy_average()
+        ug = s.unlift_average().reshape(-1).astype(np.float64)
+    eo = O.energy(P, A)
+    for g, o in zip(eg, eo):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (eg, eo)
+    rng = c["gamma_max"] - c["gamma_min"]
+    assert np.abs(ug - O.unlift(P, A.u)).max() / rng <= U_TOL
+
+
+def test_average_edge_cases():
+    """Empty average: LIFT_ERR_ARG.  One iterate: the average is that
+    iterate (its energies equal lift_energy's bit for bit).  Adding to the
+    average leaves the iterate unchanged.  Reset empties it."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(1, 13, 11, 4, 2201)
+    with gpu_solver(c) as s:
+        with pytest.raises(G.LiftError) as e:
+            s.energy_average()
+        assert e.value.code == G.LIFT_ERR_ARG
+        s.iterate(7)
+        before = s.state()
+        s.average_add()
+        after = s.state()
+        for n in before:
+            assert np.array_equal(before[n], after[n]), n
+        assert s.energy_average() == s.energy()
+        assert np.array_equal(s.unlift_average(), s.unlift())
+        s.average_reset()
+        assert s.average_count() == 0
+        with pytest.raises(G.LiftError):
+            s.unlift_average()
+
+
+def test_average_of_a_volume():
+    """On a volume the third dual component is averaged too: after one
+    iterate the averaged energies equal lift_energy's."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G, synth
+    f = torch.from_numpy(synth.as_f32(synth.voronoi_ramps_3d(4, 9, 10, 2301)[0])).cuda()
+    with G.Solver(G.LIFT_TRUNC_QUAD, 9, 10, 5, 0.0, 1.0, 0.25, 25.0, 0.1, f=f, depth=4) as s:
+        s.iterate(12)
+        s.average_add()
+        assert s.energy_average() == s.energy()
+        s.iterate(1)
+        s.average_add()
+        Pa, Da, Ea = s.energy_average()
+        assert np.isfinite([Pa, Da, Ea]).all()
