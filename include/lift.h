@@ -238,12 +238,12 @@ int lift_unlift(lift_handle h, float *out, int on_host);
  * the relaxation's optimum as well.
  *
  * lift_average(h, 1) adds the current iterate (x = {u, s}, the dual records
- * y, and pz on a volume) to the average, a <- a + (x - a) / n for the n-th
+ * y, q, and pz on a volume) to the average, a <- a + (x - a) / n for the n-th
  * iterate added; the first call after creation or after lift_average(h, 0)
  * sets a <- x.  lift_average(h, 0) empties the average (no device work).
  * The averaged records live in the handle (allocated on the first
- * accumulation: 24 bytes per (pixel, interval), 28 on a volume; LIFT_ERR_OOM
- * if that fails) and are kept apart from the iterate, which the averaging
+ * accumulation: 24 bytes per (pixel, interval), 28 on a volume, and 4 per
+ * pixel for q; LIFT_ERR_OOM if that fails) and are kept apart from the iterate, which the averaging
  * never changes.  Asynchronous on the handle's stream.  LIFT_ERR_ARG for a
  * band handle or accumulate other than 0 or 1. */
 int lift_average(lift_handle h, int accumulate);
@@ -258,6 +258,15 @@ long long lift_average_count(lift_handle h);
 int lift_energy_average(lift_handle h, double *primal_relaxed, double *dual,
                         double *e_nonconvex);
 int lift_unlift_average(lift_handle h, float *out, int on_host);
+
+/* lift_average_restart: the iterate becomes the averaged point (x and x-bar
+ * <- the average of x, the dual records and q <- their averages; the average
+ * of q is kept with the others) and the average is emptied.  A restart of
+ * the iteration from the average, as restarted primal-dual methods do on
+ * polyhedral problems; the step balance is kept, a stored unrolled forward
+ * pass is dropped.  Asynchronous.  LIFT_ERR_ARG while the average is empty or
+ * for a band handle. */
+int lift_average_restart(lift_handle h);
 
 /* State image for checkpoint / resume and for tests.  Layout (bytes, in
  * this order, all float32, pixel p = (z*H + y)*W + x, N = D*H*W, interval

@@ -77,6 +77,7 @@ struct lift_ctx {
     float2 *avg_x = nullptr;
     float4 *avg_y = nullptr;
     float *avg_pz = nullptr;
+    float *avg_q = nullptr;
     long long avg_count = 0;
 };
 
@@ -128,6 +129,7 @@ void free_ctx(lift_ctx *h)
     if (h->avg_x) cudaFree(h->avg_x);
     if (h->avg_y) cudaFree(h->avg_y);
     if (h->avg_pz) cudaFree(h->avg_pz);
+    if (h->avg_q) cudaFree(h->avg_q);
     if (h->hout) cudaFreeHost(h->hout);
     delete h;
 }
@@ -783,17 +785,22 @@ int lift_average(lift_handle h, int accumulate)
     if (!h->avg_x) {
         int rc = dev_alloc(reinterpret_cast<void **>(&h->avg_x), Nk * sizeof(float2));
         if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&h->avg_y), Nk * sizeof(float4));
+        if (rc == LIFT_OK) rc = dev_alloc(reinterpret_cast<void **>(&h->avg_q), h->N * sizeof(float));
         if (rc == LIFT_OK && h->S.pz) rc = dev_alloc(reinterpret_cast<void **>(&h->avg_pz), Nk * sizeof(float));
         if (rc != LIFT_OK) {
-            if (h->avg_x) cudaFree(h->avg_x);
-            if (h->avg_y) cudaFree(h->avg_y);
+            void *ps[] = {h->avg_x, h->avg_y, h->avg_q, h->avg_pz};
+            for (void *q : ps)
+                if (q) cudaFree(q);
             h->avg_x = nullptr;
             h->avg_y = nullptr;
+            h->avg_q = nullptr;
+            h->avg_pz = nullptr;
             return rc;
         }
     }
     const long long c = h->avg_count + 1;
-    LIFT_CK(lift::launch_average(h->S, h->avg_x, h->avg_y, h->avg_pz, Nk,
+    LIFT_CK(lift::launch_average(h->S, h->avg_x, h->avg_y, h->avg_pz, h->avg_q, Nk,
+                                 static_cast<size_t>(h->N),
                                  static_cast<float>(1.0 / static_cast<double>(c)), c == 1,
                                  h->stream));
     h->avg_count = c;
@@ -830,6 +837,27 @@ int lift_energy_average(lift_handle h, double *primal_relaxed, double *dual, dou
     if (dual) *dual = h->hout[1];
     if (e_nonconvex) *e_nonconvex = h->hout[2];
     if (!is_finite(h->hout[0]) || !is_finite(h->hout[1]) || !is_finite(h->hout[2])) return LIFT_ERR_NAN;
+    return LIFT_OK;
+}
+
+int lift_average_restart(lift_handle h)
+{
+    if (!h || h->band || h->avg_count < 1) return LIFT_ERR_ARG;
+    invalidate_unrolled(h);
+    const size_t Nk = static_cast<size_t>(h->N) * h->k;
+    LIFT_CK(cudaMemcpyAsync(h->S.x, h->avg_x, Nk * sizeof(float2), cudaMemcpyDeviceToDevice,
+                            h->stream));
+    LIFT_CK(cudaMemcpyAsync(h->S.xbar, h->avg_x, Nk * sizeof(float2), cudaMemcpyDeviceToDevice,
+                            h->stream));
+    LIFT_CK(cudaMemcpyAsync(h->S.y, h->avg_y, Nk * sizeof(float4), cudaMemcpyDeviceToDevice,
+                            h->stream));
+    LIFT_CK(cudaMemcpyAsync(h->S.q, h->avg_q, h->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                            h->stream));
+    if (h->S.pz)
+        LIFT_CK(cudaMemcpyAsync(h->S.pz, h->avg_pz, Nk * sizeof(float),
+                                cudaMemcpyDeviceToDevice, h->stream));
+    h->prev_valid = false;
+    h->avg_count = 0;
     return LIFT_OK;
 }
 

@@ -156,10 +156,10 @@ cudaError_t launch_unlift(const LiftParams &P, const float2 *x, float *out, cuda
 // current steps are those of balance theta).
 cudaError_t launch_movement(const LiftParams &P, const LiftState &S, const LiftState &Sprev,
                             float theta, double *partial, double *out, cudaStream_t st);
-// a <- a + w (x - a) over the records of S.x, S.y (and S.pz when apz is not
-// null); first: a <- x.
-cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *apz, size_t nk,
-                           float w, bool first, cudaStream_t st);
+// a <- a + w (x - a) over the nk records of S.x, S.y (and S.pz when apz is
+// not null) and the npix values of S.q; first: a <- x.
+cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *apz, float *aq,
+                           size_t nk, size_t npix, float w, bool first, cudaStream_t st);
 cudaError_t launch_proj_epi(const LiftParams &P, const int *pix, const int *interval,
                             const float *y0, const float *h0, float *y, float *h, int n,
                             cudaStream_t st);

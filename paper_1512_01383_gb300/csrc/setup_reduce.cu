@@ -410,18 +410,19 @@ cudaError_t launch_envelope(const LiftParams &P, const int *pix, const int *inte
 
 // ---------------------------------------------------------------------------
 // Running average of the iterate: a <- a + w (x - a) record by record over
-// x = {u, s}, y = {v, z, px, py} (and pz on volumes); first: a <- x (the
-// average of one iterate; the buffers' old contents are not read).  A
-// grid-stride loop over the N*k records, one float2 and one float4 each.
+// x = {u, s}, y = {v, z, px, py} (and pz on volumes), and pixel by pixel over
+// q; first: a <- x (the average of one iterate; the buffers' old contents are
+// not read).  A grid-stride loop over the N*k records and the N pixels.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 average_kernel(const float2 *__restrict__ x, const float4 *__restrict__ y,
-               const float *__restrict__ pz, float2 *__restrict__ ax, float4 *__restrict__ ay,
-               float *__restrict__ apz, size_t nk, float w, int first)
+               const float *__restrict__ pz, const float *__restrict__ q,
+               float2 *__restrict__ ax, float4 *__restrict__ ay, float *__restrict__ apz,
+               float *__restrict__ aq, size_t nk, size_t npix, float w, int first)
 {
     const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
-    for (size_t r = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; r < nk;
-         r += stride) {
+    const size_t t0 = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    for (size_t r = t0; r < nk; r += stride) {
         const float2 a = x[r];
         const float4 b = y[r];
         if (first) {
@@ -437,10 +438,12 @@ average_kernel(const float2 *__restrict__ x, const float4 *__restrict__ y,
             if (pz) apz[r] = apz[r] + w * (pz[r] - apz[r]);
         }
     }
+    for (size_t p = t0; p < npix; p += stride)
+        aq[p] = first ? q[p] : aq[p] + w * (q[p] - aq[p]);
 }
 
-cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *apz, size_t nk,
-                           float w, bool first, cudaStream_t st)
+cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *apz, float *aq,
+                           size_t nk, size_t npix, float w, bool first, cudaStream_t st)
 {
     if (nk == 0) return cudaSuccess;
     int dev = 0, sms = 0;
@@ -450,8 +453,8 @@ cudaError_t launch_average(const LiftState &S, float2 *ax, float4 *ay, float *ap
     const size_t need = (nk + 255) / 256;
     const size_t cap = static_cast<size_t>(sms) * 8;          // 8 blocks of 256 per SM
     const unsigned blocks = static_cast<unsigned>(need < cap ? need : cap);
-    average_kernel<<<blocks, 256, 0, st>>>(S.x, S.y, apz ? S.pz : nullptr, ax, ay, apz, nk, w,
-                                           first ? 1 : 0);
+    average_kernel<<<blocks, 256, 0, st>>>(S.x, S.y, apz ? S.pz : nullptr, S.q, ax, ay, apz, aq,
+                                           nk, npix, w, first ? 1 : 0);
     return cudaGetLastError();
 }
 

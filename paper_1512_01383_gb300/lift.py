@@ -36,6 +36,7 @@ EXPORTED = (
     "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
     "lift_cuda_error", "lift_batch_streams",
     "lift_average", "lift_average_count", "lift_energy_average", "lift_unlift_average",
+    "lift_average_restart",
 )
 
 
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         "lift_average_count": (C.c_longlong, [vp]),
         "lift_energy_average": (C.c_int, [vp, dp, dp, dp]),
         "lift_unlift_average": (C.c_int, [vp, vp, C.c_int]),
+        "lift_average_restart": (C.c_int, [vp]),
         "lift_state_bytes": (C.c_size_t, [vp]),
         "lift_get_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
         "lift_set_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
@@ -289,6 +291,10 @@ def lift_unlift_average(h: int, out) -> None:
            "lift_unlift_average")
 
 
+def lift_average_restart(h: int) -> None:
+    _check(load().lift_average_restart(C.c_void_p(h)), "lift_average_restart")
+
+
 def lift_state_bytes(h: int) -> int:
     return load().lift_state_bytes(C.c_void_p(h))
 
@@ -451,6 +457,10 @@ class Solver:
 
     def energy_average(self):
         return lift_energy_average(self.h)
+
+    def average_restart(self):
+        """Restart the iteration from the averaged point (and empty the average)."""
+        lift_average_restart(self.h)
 
     def unlift_average(self, out=None) -> np.ndarray:
         if out is None:

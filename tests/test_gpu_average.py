@@ -85,3 +85,38 @@ def test_average_of_a_volume():
         s.average_add()
         Pa, Da, Ea = s.energy_average()
         assert np.isfinite([Pa, Da, Ea]).all()
+
+
+@pytest.mark.parametrize("kind,H,W,L", [(2, 17, 21, 6), (1, 19, 23, 5)])
+def test_restart_from_average_matches_oracle(kind, H, W, L):
+    """Ten iterations, two epochs of fifteen iterations each averaged and
+    followed by a restart from the average, then ten plain iterations, on
+    both sides (the oracle restarts by taking its averaged state as the
+    iterate): energies within E_TOL, the unlifted image within U_TOL."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G
+    c = case(kind, H, W, L, 2400 + 10 * kind + L)
+    P, X = oracle_run(c, 10)
+    for _ in range(2):
+        X = O.pdhg_averaged(P, X, 15)
+    O.pdhg(P, X, 10)
+    with gpu_solver(c) as s:
+        with pytest.raises(G.LiftError) as e:
+            s.average_restart()                  # empty average
+        assert e.value.code == G.LIFT_ERR_ARG
+        s.iterate(10)
+        for _ in range(2):
+            s.average_reset()
+            for _ in range(15):
+                s.iterate(1)
+                s.average_add()
+            s.average_restart()
+            assert s.average_count() == 0
+        s.iterate(10)
+        eg = s.energy()
+        ug = s.unlift().reshape(-1).astype(np.float64)
+    eo = O.energy(P, X)
+    for g, o in zip(eg, eo):
+        assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (eg, eo)
+    rng = c["gamma_max"] - c["gamma_min"]
+    assert np.abs(ug - O.unlift(P, X.u)).max() / rng <= U_TOL
