@@ -73,7 +73,8 @@ def test_average_edge_cases():
 
 def test_average_of_a_volume():
     """On a volume the third dual component is averaged too: after one
-    iterate the averaged energies equal lift_energy's."""
+    iterate the averaged energies equal lift_energy's, and after a restart
+    the iterate's energies equal those of the average it was given."""
     _require_gpu()
     from paper_1512_01383_gb300 import lift as G, synth
     f = torch.from_numpy(synth.as_f32(synth.voronoi_ramps_3d(4, 9, 10, 2301)[0])).cuda()
@@ -85,6 +86,11 @@ def test_average_of_a_volume():
         s.average_add()
         Pa, Da, Ea = s.energy_average()
         assert np.isfinite([Pa, Da, Ea]).all()
+        # a restart makes the averaged point (pz included) the iterate
+        s.average_restart()
+        assert s.energy() == (Pa, Da, Ea)
+        s.iterate(5)
+        assert np.isfinite(s.energy()).all()
 
 
 @pytest.mark.parametrize("kind,H,W,L", [(2, 17, 21, 6), (1, 19, 23, 5)])
