@@ -268,6 +268,24 @@ int lift_unlift_average(lift_handle h, float *out, int on_host);
  * for a band handle. */
 int lift_average_restart(lift_handle h);
 
+/* lift_solve_averaged: lift_solve with certificates from the averaged
+ * iterate and restarts from it, for problems whose last iterate's bounds
+ * oscillate (the sampled costs of Sec. 5.4).  Epochs of first_epoch,
+ * 2 first_epoch, 4 first_epoch, ... iterations (the last clipped to
+ * max_iters); within an epoch the iterate is added to the running average
+ * (lift_average) after every `every` iterations; at the epoch's end the
+ * relative gaps (as lift_gap) of the average and of the last iterate are
+ * compared, and when the average's is the smaller the iteration restarts
+ * from it (lift_average_restart), so the iterate is always the better of
+ * the two points.  Returns LIFT_OK once that gap is <= rel_gap_tol,
+ * LIFT_ERR_NOT_CONVERGED after max_iters.  *iters_done: iterations run;
+ * *rel_gap: the iterate's relative gap at the last epoch end (either may be
+ * NULL).  The step balance stays fixed (adaptive_balance is not applied).
+ * Synchronises at every epoch end.  LIFT_ERR_ARG: null or band handle,
+ * max_iters < 0, rel_gap_tol <= 0, every < 1 or first_epoch < every. */
+int lift_solve_averaged(lift_handle h, int max_iters, double rel_gap_tol, int first_epoch,
+                        int every, int *iters_done, double *rel_gap);
+
 /* State image for checkpoint / resume and for tests.  Layout (bytes, in
  * this order, all float32, pixel p = (z*H + y)*W + x, N = D*H*W, interval
  * i = 0..k-1):

@@ -920,6 +920,46 @@ int lift_solve(lift_handle h, int max_iters, double rel_gap_tol, int *iters_done
     return LIFT_ERR_NOT_CONVERGED;
 }
 
+int lift_solve_averaged(lift_handle h, int max_iters, double rel_gap_tol, int first_epoch,
+                        int every, int *iters_done, double *rel_gap)
+{
+    if (!h || h->band || max_iters < 0 || !(rel_gap_tol > 0.0) || every < 1 ||
+        first_epoch < every)
+        return LIFT_ERR_ARG;
+    if (iters_done) *iters_done = 0;
+    int done = 0;
+    long long epoch = first_epoch;
+    while (done < max_iters) {
+        const int end = static_cast<int>(std::min<long long>(done + epoch, max_iters));
+        int rc = lift_average(h, 0);
+        if (rc != LIFT_OK) return rc;
+        while (done < end) {
+            const int step = std::min(every, end - done);
+            rc = lift_iterate(h, step);
+            if (rc != LIFT_OK) return rc;
+            rc = lift_average(h, 1);
+            if (rc != LIFT_OK) return rc;
+            done += step;
+        }
+        if (iters_done) *iters_done = done;
+        double gl = 0.0, pa = 0.0, da = 0.0;
+        rc = lift_gap(h, &gl);
+        if (rc != LIFT_OK) return rc;
+        rc = lift_energy_average(h, &pa, &da, nullptr);
+        if (rc != LIFT_OK) return rc;
+        const double ga = (pa - da) / std::max(std::max(fabs(pa), fabs(da)), 1.0);
+        if (ga < gl) {
+            rc = lift_average_restart(h);     // the iterate becomes the better point
+            if (rc != LIFT_OK) return rc;
+        }
+        const double g = std::min(ga, gl);
+        if (rel_gap) *rel_gap = g;
+        if (g <= rel_gap_tol) return LIFT_OK;
+        epoch *= 2;
+    }
+    return LIFT_ERR_NOT_CONVERGED;
+}
+
 int lift_set_bands(lift_handle h, int bands, int *used)
 {
     if (!h || bands < 0) return LIFT_ERR_ARG;

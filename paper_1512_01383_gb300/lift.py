@@ -36,7 +36,7 @@ EXPORTED = (
     "lift_create_band", "lift_band_halo_bytes", "lift_band_export", "lift_band_import",
     "lift_cuda_error", "lift_batch_streams",
     "lift_average", "lift_average_count", "lift_energy_average", "lift_unlift_average",
-    "lift_average_restart",
+    "lift_average_restart", "lift_solve_averaged",
 )
 
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "lift_energy_average": (C.c_int, [vp, dp, dp, dp]),
         "lift_unlift_average": (C.c_int, [vp, vp, C.c_int]),
         "lift_average_restart": (C.c_int, [vp]),
+        "lift_solve_averaged": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.c_int, ip, dp]),
         "lift_state_bytes": (C.c_size_t, [vp]),
         "lift_get_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
         "lift_set_state": (C.c_int, [vp, vp, C.c_size_t, C.c_int]),
@@ -295,6 +296,17 @@ def lift_average_restart(h: int) -> None:
     _check(load().lift_average_restart(C.c_void_p(h)), "lift_average_restart")
 
 
+def lift_solve_averaged(h: int, max_iters: int, rel_gap_tol: float, first_epoch: int = 1000,
+                        every: int = 10) -> tuple[int, int, float]:
+    """(return code LIFT_OK or LIFT_ERR_NOT_CONVERGED, iterations, final gap)."""
+    n, g = C.c_int(0), C.c_double(float("nan"))
+    rc = load().lift_solve_averaged(C.c_void_p(h), max_iters, rel_gap_tol, first_epoch, every,
+                                    C.byref(n), C.byref(g))
+    if rc not in (LIFT_OK, LIFT_ERR_NOT_CONVERGED):
+        _check(rc, "lift_solve_averaged")
+    return rc, n.value, g.value
+
+
 def lift_state_bytes(h: int) -> int:
     return load().lift_state_bytes(C.c_void_p(h))
 
@@ -457,6 +469,10 @@ class Solver:
 
     def energy_average(self):
         return lift_energy_average(self.h)
+
+    def solve_averaged(self, max_iters: int, rel_gap_tol: float, first_epoch: int = 1000,
+                       every: int = 10):
+        return lift_solve_averaged(self.h, max_iters, rel_gap_tol, first_epoch, every)
 
     def average_restart(self):
         """Restart the iteration from the averaged point (and empty the average)."""

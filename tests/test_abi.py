@@ -108,6 +108,7 @@ def test_null_arguments(lib):
     assert L.lift_energy_average(None, None, None, None) == lib.LIFT_ERR_ARG
     assert L.lift_unlift_average(None, None, 0) == lib.LIFT_ERR_ARG
     assert L.lift_average_restart(None) == lib.LIFT_ERR_ARG
+    assert L.lift_solve_averaged(None, 10, 1e-3, 10, 1, None, None) == lib.LIFT_ERR_ARG
 
 
 def test_volume_batch_rejected_before_any_cuda_call(lib):

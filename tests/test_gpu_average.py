@@ -126,3 +126,35 @@ def test_restart_from_average_matches_oracle(kind, H, W, L):
         assert abs(g - o) <= E_TOL * max(abs(o), 1.0), (eg, eo)
     rng = c["gamma_max"] - c["gamma_min"]
     assert np.abs(ug - O.unlift(P, X.u)).max() / rng <= U_TOL
+
+
+def test_solve_averaged_certifies_in_fp64():
+    """An 8 x 8 crop of the stereo cost volume (65 disparities, L = 8,
+    balance 0.1), where the last iterate's gap stalls near 0.08:
+    lift_solve_averaged reaches gap 5e-3, the gap it returns is the iterate's
+    own (lift_gap agrees bit for bit), and the oracle's FP64 energies of the
+    final state certify it; lift_solve on the last iterate needs more
+    iterations or does not get there."""
+    _require_gpu()
+    from paper_1512_01383_gb300 import lift as G, synth
+    cost, _ = synth.stereo_cost(480, 640, synth.BASE_SEED + 3, ndisp=65)
+    c32 = np.ascontiguousarray(synth.as_f32(cost)[:8, :8])
+    cd = torch.from_numpy(c32).cuda()
+    tol, cap = 5e-3, 200000
+    kw = dict(cost=cd, sample_min=0.0, sample_max=64.0, step_balance=0.1)
+    with G.Solver(G.LIFT_PL_SAMPLED, 8, 8, 8, 0.0, 64.0, 0.05, **kw) as s:
+        rc, n, g = s.solve_averaged(cap, tol, first_epoch=1000, every=10)
+        assert rc == G.LIFT_OK, (rc, n, g)
+        assert g <= tol and s.gap() == g
+        st = s.state()
+    with G.Solver(G.LIFT_PL_SAMPLED, 8, 8, 8, 0.0, 64.0, 0.05, **kw) as s:
+        rc_plain, n_plain = s.solve(cap, tol)
+    assert rc_plain != G.LIFT_OK or n_plain > n, (n, n_plain)
+    P = O.Problem(O.PL, 8, 8, 8, 0.0, 64.0, lam=0.05, cost=c32.astype(np.float64),
+                  smin=0.0, smax=64.0, theta=0.1)
+    X = O.State(P)
+    for name in ("u", "s", "v", "z", "px", "py"):
+        getattr(X, name)[...] = st[name].reshape(P.N, P.k)
+    X.q[...] = st["q"].reshape(P.N)
+    Ph, D, _ = O.energy(P, X)
+    assert (Ph - D) / max(abs(Ph), abs(D), 1.0) <= tol + 1e-4, (Ph, D)
