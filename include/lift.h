@@ -244,8 +244,10 @@ int lift_unlift(lift_handle h, float *out, int on_host);
  * The averaged records live in the handle (allocated on the first
  * accumulation: 24 bytes per (pixel, interval), 28 on a volume, and 4 per
  * pixel for q; LIFT_ERR_OOM if that fails) and are kept apart from the iterate, which the averaging
- * never changes.  Asynchronous on the handle's stream.  LIFT_ERR_ARG for a
- * band handle or accumulate other than 0 or 1. */
+ * never changes.  lift_reset, lift_set_data and lift_set_params empty the
+ * average too (its points belong to the old start or problem).
+ * Asynchronous on the handle's stream.  LIFT_ERR_ARG for a band handle or
+ * accumulate other than 0 or 1. */
 int lift_average(lift_handle h, int accumulate);
 
 /* The number of iterates in the average (0 after lift_average(h, 0)); -1 for

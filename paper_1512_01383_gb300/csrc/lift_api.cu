@@ -569,6 +569,7 @@ static void invalidate_unrolled(lift_handle h)
 {
     h->unrolled_iters = 0;
     ++h->generation;
+    h->avg_count = 0;   // the running average belongs to the old problem or start
 }
 
 int lift_set_data(lift_handle h, const float *data, int on_host)

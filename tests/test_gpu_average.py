@@ -49,7 +49,8 @@ def test_average_matches_oracle(kind, H, W, L):
 def test_average_edge_cases():
     """Empty average: LIFT_ERR_ARG.  One iterate: the average is that
     iterate (its energies equal lift_energy's bit for bit).  Adding to the
-    average leaves the iterate unchanged.  Reset empties it."""
+    average leaves the iterate unchanged.  average_reset and lift_reset
+    empty it."""
     _require_gpu()
     from paper_1512_01383_gb300 import lift as G
     c = case(1, 13, 11, 4, 2201)
@@ -69,6 +70,11 @@ def test_average_edge_cases():
         assert s.average_count() == 0
         with pytest.raises(G.LiftError):
             s.unlift_average()
+        # a fresh start empties the average
+        s.average_add()
+        assert s.average_count() == 1
+        s.reset()
+        assert s.average_count() == 0
 
 
 def test_average_of_a_volume():
