@@ -9,5 +9,5 @@ from .oracle import (  # noqa: F401
     QUAD, TRUNC, PL, PERIODIC, Problem, State, build, conj, lifted_conj, proj_epi, biconj,
     rho, grad, div, steps, pdhg, unlift, monotone_proj, energy, rof_direct,
     rof_energy, labels, unrolled_grad, movement, pdhg_adaptive, grad3, div3, rof_direct3,
-    rof_energy3, half_step, pdhg_averaged,
+    rof_energy3, half_step, pdhg_averaged, solve_restarted,
 )

@@ -402,3 +402,53 @@ def pdhg_averaged(P: Problem, X: State, iters: int, every: int = 1) -> State:
     A.ubar[...] = A.u
     A.sbar[...] = A.s
     return A
+
+
+def solve_restarted(P: Problem, X: State, max_iters: int, rel_gap_tol: float, beta: float = 0.5,
+                    every: int = 10, check: int = 500):
+    """Primal-dual iterations with restarts from the averaged iterate.  The
+    iterate is added to a running average every `every` iterations; every
+    `check` iterations the relative gaps (P_hat - D) / max(|P_hat|, |D|, 1)
+    of the average and of the last iterate are compared, and once the
+    smaller is at most beta times the gap at the previous restart, the
+    better point becomes the iterate (its extrapolated point its own x) and
+    the average starts afresh.  Stops when that smaller gap is <= rel_gap_tol.
+    Returns (X, iterations done, the best gap, restarts)."""
+    names = ("u", "s", "v", "z", "px", "py", "pz", "q")
+
+    def rel_gap(S):
+        p, d, _ = energy(P, S)
+        return (p - d) / max(abs(p), abs(d), 1.0)
+
+    acc = {n: np.zeros_like(getattr(X, n)) for n in names}
+    cnt, done, restarts = 0, 0, 0
+    g_restart, best = float("inf"), float("inf")
+    while done < max_iters:
+        for _ in range(max(check // every, 1)):
+            if done >= max_iters:
+                break
+            step = min(every, max_iters - done)
+            pdhg(P, X, step)
+            done += step
+            for n in names:
+                acc[n] += getattr(X, n)
+            cnt += 1
+        A = State(P)
+        for n in names:
+            getattr(A, n)[...] = acc[n] / cnt
+        A.ubar[...] = A.u
+        A.sbar[...] = A.s
+        ga, gl = rel_gap(A), rel_gap(X)
+        g = min(ga, gl)
+        best = min(best, g)
+        if g <= rel_gap_tol or g <= beta * g_restart:
+            if ga < gl:
+                X = A
+            g_restart = g
+            restarts += 1
+            for n in names:
+                acc[n][...] = 0.0
+            cnt = 0
+            if g <= rel_gap_tol:
+                break
+    return X, done, best, restarts
